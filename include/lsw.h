@@ -1,0 +1,204 @@
+/*
+ * lsw.h -- C ABI of a GB300 (sm_103a) solver for the 2D acoustic
+ * Lippmann-Schwinger equation  (I - G0 V) psi = psi0  by the preconditioned
+ * scattering series of Eikrem, Naevdal and Jakobsen, "Iterative solution of
+ * the Lippmann-Schwinger equation in strongly scattering acoustic media by
+ * randomized construction of preconditioners" (arXiv:2005.01372).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid.      nz x nx cells of size h x h.  Unknowns are ordered in vertical
+ *            strips (Sec. 2.4): the linear index of cell (iz, ix) is
+ *            ix * nz + iz.  nz and nx must be powers of two, 1 <= n <= 2048.
+ * Complex.   Interleaved (re, im): LSW_C128 = two doubles, LSW_C64 = two
+ *            floats.  A batch of nbatch fields is stored field after field,
+ *            stride nz * nx elements.
+ * Contrast.  chi is always a device array of nz * nx doubles, Eq. 1:
+ *            chi = w^2 (1/c^2 - 1/c0^2).
+ * Green.     G0(r) = (i/4) H0^(1)(k0 r), k0 = 2 pi f / c0 (time dependence
+ *            exp(-i w t)).  Each cell is integrated over the disk of equal
+ *            area, so the cell volume of Eq. 4 is inside the Green table and
+ *            V = diag(chi).
+ * Pointers.  Unless a parameter says "host", every array pointer is a device
+ *            pointer owned by the caller.  Handles (lsw_green, lsw_hmatrix)
+ *            are owned by the library; free them with lsw_destroy_*.
+ * Streams.   Every call takes a cudaStream_t (passed as void*; NULL = the
+ *            legacy default stream) and is asynchronous on it, except where
+ *            stated.  Calls allocate their scratch with cudaMallocAsync on
+ *            that stream.
+ * Errors.    Calls return an lsw_status.  On failure outputs are unspecified
+ *            and handles stay valid.  No call exits, aborts or traps.
+ *            Calls on one handle are not thread-safe.
+ */
+#ifndef LSW_H
+#define LSW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lsw_status;
+enum {
+    LSW_OK = 0,
+    LSW_ERR_INVALID_ARG = 1,      /* NULL pointer, bad enum, bad size        */
+    LSW_ERR_UNSUPPORTED_SIZE = 2, /* grid not a power of two or too large    */
+    LSW_ERR_OOM = 3,              /* device allocation failed                */
+    LSW_ERR_CUDA = 4,             /* a CUDA runtime call failed              */
+    LSW_ERR_NOT_CONVERGED = 5,    /* max_iter reached above the tolerance    */
+    LSW_ERR_DIVERGED = 6,         /* residual grew 1e3x above its minimum    */
+    LSW_ERR_NUMERIC = 7,          /* NaN or Inf met                          */
+    LSW_ERR_TIMEOUT = 8           /* reserved for bounded device-side waits  */
+};
+
+typedef enum { LSW_C128 = 0, LSW_C64 = 1, LSW_MIXED = 2 } lsw_prec;
+
+/* Products computed by lsw_apply_operator (Eq. 4, Eq. 13, Algorithm 2). */
+typedef enum {
+    LSW_OP_FORWARD = 0,   /* y = u0 + G0 V u                                 */
+    LSW_OP_RESIDUAL = 1,  /* y = u - G0 V u - u0   (a_{j-1} of Eq. 13)        */
+    LSW_OP_PLAIN = 2,     /* y = G0 V u                                      */
+    LSW_OP_ADJOINT = 3    /* y = (G0 V)^H u = chi . conj(G0 conj(u))          */
+} lsw_op_mode;
+
+typedef struct {
+    int32_t nz, nx;       /* cells in depth (z) and horizontally (x)         */
+    double h;             /* cell size [m]                                   */
+    double c0;            /* background velocity [m/s] (Eq. 1)               */
+    double freq_hz;       /* frequency f, w = 2 pi f                         */
+} lsw_grid;
+
+/* A rectangle of cells [z0, z1) x [x0, x1). */
+typedef struct { int32_t z0, z1, x0, x1; } lsw_box;
+
+typedef struct lsw_green lsw_green;       /* Green table + spectra, opaque   */
+typedef struct lsw_hmatrix lsw_hmatrix;   /* preconditioner H, opaque        */
+
+typedef enum { LSW_H_LOWRANK_SMW = 0, LSW_H_HODLR = 1 } lsw_h_kind;
+typedef enum { LSW_SPLIT_QUADTREE = 0, LSW_SPLIT_STRIPS = 1 } lsw_split;
+
+typedef struct {
+    int32_t kind;         /* lsw_h_kind                                       */
+    int32_t prec;         /* LSW_C128 or LSW_C64: storage and arithmetic of H */
+    int32_t levels;       /* HODLR: levels of the cluster tree (leaves at L)  */
+    int32_t split;        /* HODLR: lsw_split                                 */
+    int32_t rank;         /* r, the same for every low-rank block (Sec. 2.4)  */
+    int32_t oversample;   /* extra probes p: r + p Gaussian columns           */
+    int32_t q;            /* power iterations of Algorithm 2 (0 on the paper's HODLR path) */
+    int32_t pad_;
+    uint64_t seed;        /* Philox4x32-10 key of every probe block           */
+} lsw_hparams;
+
+typedef struct {
+    int32_t prec;         /* LSW_C128, LSW_C64 or LSW_MIXED                    */
+    int32_t max_iter;     /* series steps per solve (30 in Sec. 3.1)           */
+    double tol;           /* stop when ||psi0 - (I - G0V) psi||_2 <= tol ||psi0||_2 */
+    double inner_tol;     /* LSW_MIXED: relative tolerance of each FP32 inner solve */
+    int32_t max_outer;    /* LSW_MIXED: refinement steps                       */
+    int32_t pad_;
+} lsw_solve_params;
+
+typedef struct {
+    int32_t iterations;   /* series steps taken (inner steps summed for MIXED) */
+    int32_t outer;        /* refinement steps (MIXED), else 0                  */
+    int32_t status;       /* LSW_OK, LSW_ERR_NOT_CONVERGED, ...                */
+    int32_t pad_;
+    double rel_residual;  /* final ||psi0 - (I - G0V) psi|| / ||psi0||, FP64   */
+} lsw_solve_info;
+
+/* Text for a status code (static storage). */
+const char* lsw_status_string(lsw_status s);
+/* Text of the last CUDA failure seen by the calling thread (diagnostics). */
+const char* lsw_last_error(void);
+
+/* Green table and spectra (Sec. 2.2).
+ * Tabulates the cell-integrated Green's function Gt at every offset
+ * 0 <= dz <= nz, 0 <= dx <= nx in FP64 (Bessel J0, J1, Y0, Y1), builds its
+ * even circulant extension to 2nz x 2nx (the paper cites Nowak et al. 2003
+ * for the extension; index N holds the offset-N value so the extension is
+ * exactly even), and stores its 2D FFT, scaled by 1 / (4 nz nx), as the
+ * (nz + 1) x (nx + 1) quarter that evenness allows, in FP64 and FP32.
+ * *out receives a new handle.  Not asynchronous: returns after the build. */
+lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out);
+lsw_status lsw_destroy_green(lsw_green* g);
+
+/* Copies of the handle's tables, for checking.
+ * table: (nx + 1) x (nz + 1) complex doubles, entry dx * (nz + 1) + dz.
+ * spectrum: the scaled quarter spectrum, same shape and layout, kx-major. */
+lsw_status lsw_green_table(const lsw_green* g, void* table_c128, void* stream);
+lsw_status lsw_green_spectrum(const lsw_green* g, void* spec_c128, void* stream);
+
+/* Eq. 1: chi = w^2 (1/c^2 - 1/c0^2) for every cell.
+ * velocity, chi: device arrays of nz * nx doubles (may alias). */
+lsw_status lsw_contrast(const lsw_green* g, const double* velocity, double* chi, void* stream);
+
+/* Background fields psi0 of unit point sources, one field per source:
+ * psi0_i = Gt(r_i) / h^2, i.e. (i/4) H0(k0 r) 2 J1(k0 a)/(k0 a) off the
+ * source cell, a = h / sqrt(pi).
+ * positions: HOST array of 2 * nsrc int32, (iz, ix) per source.
+ * u0: nsrc fields of precision prec (LSW_C128 or LSW_C64). */
+lsw_status lsw_point_sources(const lsw_green* g, const int32_t* positions, int nsrc,
+                             int prec, void* u0, void* stream);
+
+/* The Lippmann-Schwinger operator through zero-padded FFTs (Sec. 2.2,
+ * Eq. 4): for each of nbatch fields computes the product named by mode
+ * (lsw_op_mode).  prec: LSW_C128 or LSW_C64 for u, u0 and y.  u0 may be
+ * NULL for FORWARD and RESIDUAL (read as zero) and is ignored otherwise.
+ * y must not alias u or u0.  Scratch: 2 * nbatch * nz * nx complex. */
+lsw_status lsw_apply_operator(const lsw_green* g, int prec, const double* chi,
+                              const void* u, const void* u0, void* y,
+                              int nbatch, int mode, void* stream);
+
+/* Randomized range sketch of one block of G0 V (Algorithm 2): with s =
+ * rows and t = cols (boxes inside the grid, unknowns numbered in strip order
+ * inside each box), computes U (n_s x rank) and W (n_t x rank), column-major,
+ * with (G0 V)[s, t] ~ U W^H.  Probes: rank + oversample complex Gaussian
+ * columns from Philox4x32-10 keyed by seed, stream words (2 << 28, stream).
+ * q power iterations.  Products by FFT on the bounding box of s and t.
+ * prec: LSW_C128 or LSW_C64 for U and W.  Columns beyond the numerical rank
+ * are zero.  The factors are unique only up to U W^H. */
+lsw_status lsw_sketch_range(const lsw_green* g, int prec, const double* chi,
+                            lsw_box rows, lsw_box cols, int rank, int oversample, int q,
+                            uint64_t seed, uint32_t stream_id, void* U, void* W, void* stream);
+
+/* Preconditioner H ~ (I - G0 V)^-1 (Sec. 2.3-2.4).
+ * kind LSW_H_LOWRANK_SMW: G0 V ~ U W^H over the whole grid (Algorithm 2) and
+ *   H = I + U (I_r - W^H U)^-1 W^H (Eq. 12).
+ * kind LSW_H_HODLR: randomized HODLR approximation of I - G0 V (off-diagonal
+ *   blocks by Algorithm 2 on each parent box, dense diagonal leaves), then
+ *   its inverse by the recursive 2x2 block-inverse formula with randomized
+ *   rank-r recompression of every low-rank sum (Algorithm 1, q = 0).
+ * The handle keeps its own copy of what it needs (not chi).  *out receives
+ * the handle.  Returns after the build (synchronises the stream). */
+lsw_status lsw_build_hmatrix(const lsw_green* g, const double* chi, const lsw_hparams* hp,
+                             void* stream, lsw_hmatrix** out);
+lsw_status lsw_destroy_hmatrix(lsw_hmatrix* h);
+/* Device bytes held by the handle. */
+lsw_status lsw_hmatrix_bytes(const lsw_hmatrix* h, uint64_t* bytes);
+
+/* y = H x for nbatch fields in the grid's strip ordering, in H's precision
+ * (hp->prec).  x and y must not alias. */
+lsw_status lsw_apply_precond(const lsw_hmatrix* h, const void* x, void* y, int nbatch, void* stream);
+
+/* Solve (I - G0 V) psi = psi0 for nbatch right-hand sides by the scattering
+ * series of Eq. 11, psi_j = psi_{j-1} - H (psi_{j-1} - G0 V psi_{j-1} - psi0),
+ * started from psi_0 = H psi0.  H == NULL gives the Born series started from
+ * psi0 (Sec. 2.2).  Each source stops once its FP64 relative residual is at
+ * most sp->tol (Sec. 3.2 stopping rule, read as relative).
+ * prec LSW_C128 / LSW_C64: everything in that precision, u0 and u too.
+ * prec LSW_MIXED: u0 and u are LSW_C128; iterative refinement -- the FP64
+ *   residual r = psi0 - (I - G0 V) psi is formed in FP64, the correction
+ *   (I - G0 V) d = r is solved by the series in FP32 (H must be LSW_C64) to
+ *   sp->inner_tol, and psi += d, until the FP64 residual meets sp->tol.
+ * info: HOST array of nbatch records.  Synchronises the stream (once per
+ * series step to read the residual norms).  Returns LSW_OK when every source
+ * converged, else the first failing source's status. */
+lsw_status lsw_solve_series(const lsw_green* g, const double* chi, const lsw_hmatrix* h,
+                            const void* u0, void* u, int nbatch, const lsw_solve_params* sp,
+                            lsw_solve_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSW_H */

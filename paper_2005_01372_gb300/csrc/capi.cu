@@ -1,0 +1,136 @@
+// extern "C" entry points of lsw.h: argument checks, then the internal calls.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lsw_internal.cuh"
+
+namespace lsw {
+
+static thread_local char g_last_error[512];
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+lsw_status green_init(lsw_green* g, cudaStream_t st);
+lsw_status contrast(const lsw_green* g, const double* vel, double* chi, cudaStream_t st);
+lsw_status point_sources(const lsw_green* g, const int32_t* pos_host, int nsrc, int prec, void* u0,
+                         cudaStream_t st);
+
+}  // namespace lsw
+
+using namespace lsw;
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static bool grid_ok(int n) { return n >= 1 && n <= 2048 && is_pow2(n); }
+
+extern "C" {
+
+const char* lsw_status_string(lsw_status s) {
+    switch (s) {
+        case LSW_OK: return "ok";
+        case LSW_ERR_INVALID_ARG: return "invalid argument";
+        case LSW_ERR_UNSUPPORTED_SIZE: return "unsupported size (grid sides must be powers of two <= 2048)";
+        case LSW_ERR_OOM: return "device allocation failed";
+        case LSW_ERR_CUDA: return "CUDA runtime error";
+        case LSW_ERR_NOT_CONVERGED: return "not converged within max_iter";
+        case LSW_ERR_DIVERGED: return "diverged";
+        case LSW_ERR_NUMERIC: return "NaN or Inf";
+        case LSW_ERR_TIMEOUT: return "timeout";
+        default: return "unknown status";
+    }
+}
+
+// Last CUDA error text of the calling thread (not part of lsw.h's contract
+// beyond diagnostics).
+const char* lsw_last_error(void) { return g_last_error; }
+
+lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out) {
+    if (!grid || !out) return LSW_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid_ok(grid->nz) || !grid_ok(grid->nx)) return LSW_ERR_UNSUPPORTED_SIZE;
+    if (!(grid->h > 0) || !(grid->c0 > 0) || !(grid->freq_hz > 0) || !std::isfinite(grid->h) ||
+        !std::isfinite(grid->c0) || !std::isfinite(grid->freq_hz))
+        return LSW_ERR_INVALID_ARG;
+    lsw_green* g = new (std::nothrow) lsw_green();
+    if (!g) return LSW_ERR_OOM;
+    cudaGetDevice(&g->device);
+    g->nz = grid->nz;
+    g->nx = grid->nx;
+    g->h = grid->h;
+    g->c0 = grid->c0;
+    g->freq = grid->freq_hz;
+    g->k = 2.0 * M_PI * grid->freq_hz / grid->c0;
+    lsw_status st = green_init(g, S(stream));
+    if (st != LSW_OK) {
+        lsw_destroy_green(g);
+        return st;
+    }
+    *out = g;
+    return LSW_OK;
+}
+
+lsw_status lsw_destroy_green(lsw_green* g) {
+    if (!g) return LSW_ERR_INVALID_ARG;
+    if (g->table) cudaFree(g->table);
+    if (g->tw64) cudaFree(g->tw64);
+    if (g->tw32) cudaFree(g->tw32);
+    free_spectrum(&g->full);
+    delete g;
+    return LSW_OK;
+}
+
+lsw_status lsw_green_table(const lsw_green* g, void* table, void* stream) {
+    if (!g || !table) return LSW_ERR_INVALID_ARG;
+    const size_t n = (size_t)(g->nz + 1) * (g->nx + 1);
+    LSW_CUDA(cudaMemcpyAsync(table, g->table, n * sizeof(double2), cudaMemcpyDeviceToDevice, S(stream)));
+    return LSW_OK;
+}
+
+lsw_status lsw_green_spectrum(const lsw_green* g, void* spec, void* stream) {
+    if (!g || !spec) return LSW_ERR_INVALID_ARG;
+    const size_t n = (size_t)(g->nz + 1) * (g->nx + 1);
+    LSW_CUDA(cudaMemcpyAsync(spec, g->full.q64, n * sizeof(double2), cudaMemcpyDeviceToDevice, S(stream)));
+    return LSW_OK;
+}
+
+lsw_status lsw_contrast(const lsw_green* g, const double* velocity, double* chi, void* stream) {
+    if (!g || !velocity || !chi) return LSW_ERR_INVALID_ARG;
+    return contrast(g, velocity, chi, S(stream));
+}
+
+lsw_status lsw_point_sources(const lsw_green* g, const int32_t* positions, int nsrc, int prec, void* u0,
+                             void* stream) {
+    if (!g || !positions || !u0 || nsrc <= 0) return LSW_ERR_INVALID_ARG;
+    if (prec != LSW_C128 && prec != LSW_C64) return LSW_ERR_INVALID_ARG;
+    return point_sources(g, positions, nsrc, prec, u0, S(stream));
+}
+
+lsw_status lsw_apply_operator(const lsw_green* g, int prec, const double* chi, const void* u, const void* u0,
+                              void* y, int nbatch, int mode, void* stream) {
+    if (!g || !chi || nbatch < 0) return LSW_ERR_INVALID_ARG;
+    if (mode < LSW_OP_FORWARD || mode > LSW_OP_ADJOINT) return LSW_ERR_INVALID_ARG;
+    if (prec != LSW_C128 && prec != LSW_C64) return LSW_ERR_INVALID_ARG;
+    if (nbatch == 0) return LSW_OK;
+    if (!u || !y || y == u || (u0 && y == u0)) return LSW_ERR_INVALID_ARG;
+    if (mode != LSW_OP_FORWARD && mode != LSW_OP_RESIDUAL) u0 = nullptr;
+    cudaStream_t st = S(stream);
+    const long long n = (long long)g->nz * g->nx;
+    OpGeom geo{g->nz, g->nx, chi, g->nz, nullptr, 1};
+    DevBuf work;
+    if (prec == LSW_C128) {
+        LSW_TRY(work.alloc(sizeof(double2) * 2 * n * nbatch, st));
+        return op_apply<double>(g, g->full, geo, mode, (const double2*)u, (const double2*)u0, (double2*)y, nbatch,
+                                work.as<double2>(), st);
+    }
+    LSW_TRY(work.alloc(sizeof(float2) * 2 * n * nbatch, st));
+    return op_apply<float>(g, g->full, geo, mode, (const float2*)u, (const float2*)u0, (float2*)y, nbatch,
+                           work.as<float2>(), st);
+}
+
+}  // extern "C"

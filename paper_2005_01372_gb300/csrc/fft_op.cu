@@ -1,0 +1,424 @@
+// The Lippmann-Schwinger operator through zero-padded FFTs (Sec. 2.2, Eq. 4),
+// and the Green table / spectra it multiplies by.
+//
+// A field on a (bz x bx) box is convolved with the Green table on the
+// (2bz x 2bx) padded grid in three passes; the padded half of each axis is
+// never stored:
+//   pass A  (per column)  chi-multiply, zero-pad, FFT along z     -> T[kz][ix]
+//   pass B  (per row kz)  zero-pad, FFT along x, multiply by the quarter
+//                         spectrum, inverse FFT along x, crop      -> T[kz][ix]
+//   pass C  (per column)  inverse FFT along z, crop, epilogue     -> y
+// T holds 2bz x bx complex per field.  The spectrum carries the 1/(4 bz bx)
+// of the inverse transform.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "fft.cuh"
+#include "lsw_internal.cuh"
+
+namespace lsw {
+
+namespace {
+
+template <typename R> struct FftCfg;
+template <> struct FftCfg<float>  { static constexpr int NT = 256, MB4 = 8; };
+template <> struct FftCfg<double> { static constexpr int NT = 256, MB4 = 4; };
+
+// elements of one CTA's line set: nlines * P <= 4 * NT * MB4
+template <typename R> constexpr int fft_capacity() { return 4 * FftCfg<R>::NT * FftCfg<R>::MB4; }
+
+struct DevGeom {
+    int bz, bx, logbz;
+    const double* chi;
+    int chi_ld;
+    const int2* origin;
+    int vpb;
+};
+
+__device__ __forceinline__ int2 box_origin(const DevGeom& g, int b) {
+    return g.origin ? g.origin[b / g.vpb] : make_int2(0, 0);
+}
+
+// ----------------------------------------------------------------- pass A
+template <typename R, int NT, int MB4>
+__global__ void __launch_bounds__(NT)
+k_pass_a(const typename Cx<R>::T* __restrict__ u, DevGeom geo, int pz, int logpz, int cx, int logcx,
+         int lstride, const typename Cx<R>::T* __restrict__ tw, int twstep, int adjoint,
+         typename Cx<R>::T* __restrict__ T) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sm = reinterpret_cast<C*>(sm_raw);
+    const int b = blockIdx.y;
+    const int ix0 = blockIdx.x * cx;
+    const int2 org = box_origin(geo, b);           // (z0, x0)
+    const long long nbox = (long long)geo.bz * geo.bx;
+    const C* ub = u + b * nbox;
+    const int tot = cx * pz;
+    for (int e = threadIdx.x; e < tot; e += NT) {
+        const int c = e >> logpz, iz = e & (pz - 1);
+        C v = czero<C>();
+        if (iz < geo.bz) {
+            const int ix = ix0 + c;
+            v = ub[(long long)ix * geo.bz + iz];
+            if (adjoint) {
+                v.y = -v.y;
+            } else {
+                const R ch = (R)geo.chi[(long long)(org.y + ix) * geo.chi_ld + org.x + iz];
+                v = cscale(v, ch);
+            }
+        }
+        sm[c * lstride + iz] = v;
+    }
+    __syncthreads();
+    smem_fft<C, NT, MB4>(sm, lstride, cx, pz, logpz, tw, twstep, false);
+    C* Tb = T + (long long)b * pz * geo.bx;
+    for (int e = threadIdx.x; e < tot; e += NT) {
+        const int kz = e >> logcx, c = e & (cx - 1);
+        Tb[(long long)kz * geo.bx + ix0 + c] = sm[c * lstride + kz];
+    }
+}
+
+// ----------------------------------------------------------------- pass B
+template <typename R, int NT, int MB4>
+__global__ void __launch_bounds__(NT)
+k_pass_b(typename Cx<R>::T* __restrict__ T, int bx, int pz, int px, int logpx, int rz, int logrz,
+         int lstride, const typename Cx<R>::T* __restrict__ specq, int qz,
+         const typename Cx<R>::T* __restrict__ tw, int twstep) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sm = reinterpret_cast<C*>(sm_raw);
+    const int b = blockIdx.y;
+    const int kz0 = blockIdx.x * rz;
+    C* Tb = T + (long long)b * pz * bx;
+    const int tot = rz * px;
+    for (int e = threadIdx.x; e < tot; e += NT) {
+        const int r = e >> logpx, ix = e & (px - 1);
+        sm[r * lstride + ix] = ix < bx ? Tb[(long long)(kz0 + r) * bx + ix] : czero<C>();
+    }
+    __syncthreads();
+    smem_fft<C, NT, MB4>(sm, lstride, rz, px, logpx, tw, twstep, false);
+    for (int e = threadIdx.x; e < tot; e += NT) {
+        const int r = e >> logpx, kx = e & (px - 1);
+        const int kz = kz0 + r;
+        const int qx = min(kx, px - kx), qzz = min(kz, pz - kz);
+        sm[r * lstride + kx] = cmul(sm[r * lstride + kx], specq[qx * qz + qzz]);
+    }
+    __syncthreads();
+    smem_fft<C, NT, MB4>(sm, lstride, rz, px, logpx, tw, twstep, true);
+    const int totc = rz * bx;
+    for (int e = threadIdx.x; e < totc; e += NT) {
+        const int r = e / bx, ix = e - r * bx;
+        Tb[(long long)(kz0 + r) * bx + ix] = sm[r * lstride + ix];
+    }
+}
+
+// ----------------------------------------------------------------- pass C
+template <typename R, int NT, int MB4>
+__global__ void __launch_bounds__(NT)
+k_pass_c(const typename Cx<R>::T* __restrict__ T, DevGeom geo, int pz, int logpz, int cx, int logcx,
+         int lstride, const typename Cx<R>::T* __restrict__ tw, int twstep, int mode,
+         const typename Cx<R>::T* __restrict__ u, const typename Cx<R>::T* __restrict__ u0,
+         typename Cx<R>::T* __restrict__ y) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sm = reinterpret_cast<C*>(sm_raw);
+    const int b = blockIdx.y;
+    const int ix0 = blockIdx.x * cx;
+    const C* Tb = T + (long long)b * pz * geo.bx;
+    const int tot = cx * pz;
+    for (int e = threadIdx.x; e < tot; e += NT) {
+        const int kz = e >> logcx, c = e & (cx - 1);
+        sm[c * lstride + kz] = Tb[(long long)kz * geo.bx + ix0 + c];
+    }
+    __syncthreads();
+    smem_fft<C, NT, MB4>(sm, lstride, cx, pz, logpz, tw, twstep, true);
+    const long long nbox = (long long)geo.bz * geo.bx;
+    const int2 org = box_origin(geo, b);
+    const int tote = cx * geo.bz;
+    for (int e = threadIdx.x; e < tote; e += NT) {
+        const int c = e >> geo.logbz, iz = e & (geo.bz - 1);
+        const int ix = ix0 + c;
+        const long long idx = b * nbox + (long long)ix * geo.bz + iz;
+        C g = sm[c * lstride + iz];
+        C out;
+        switch (mode) {
+            case LSW_OP_FORWARD:
+                out = u0 ? cadd(u0[idx], g) : g;
+                break;
+            case LSW_OP_RESIDUAL:
+                out = csub(u[idx], g);
+                if (u0) out = csub(out, u0[idx]);
+                break;
+            case LSW_OP_ADJOINT: {
+                const R ch = (R)geo.chi[(long long)(org.y + ix) * geo.chi_ld + org.x + iz];
+                out = mk(g.x * ch, -g.y * ch);
+                break;
+            }
+            default:
+                out = g;
+        }
+        y[idx] = out;
+    }
+}
+
+// ------------------------------------------------ generic strided 1D FFTs
+// nlines lines of length P: element i of line l at data[l * lstep + i * estep].
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_fft_strided64(double2* data, int P, int logP, int nlines, int lpc, long long lstep, long long estep,
+                const double2* __restrict__ tw, int twstep, int inv) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double2* sm = reinterpret_cast<double2*>(sm_raw);
+    const int l0 = blockIdx.x * lpc;
+    const int nl = min(lpc, nlines - l0);
+    for (int e = threadIdx.x; e < nl * P; e += NT) {
+        const int l = e >> logP, i = e & (P - 1);
+        sm[l * P + i] = data[(l0 + l) * lstep + i * estep];
+    }
+    __syncthreads();
+    smem_fft<double2, NT, 4>(sm, P, nl, P, logP, tw, twstep, inv != 0);
+    for (int e = threadIdx.x; e < nl * P; e += NT) {
+        const int l = e >> logP, i = e & (P - 1);
+        data[(l0 + l) * lstep + i * estep] = sm[l * P + i];
+    }
+}
+
+// ------------------------------------------------------------ Green table
+// Cell-integrated Green's function (disk of equal area, radius a):
+//   r > 0:  (i pi a / (2k)) J1(ka) H0(kr)
+//   r = 0:  (i pi a / (2k)) H1(ka) - 1/k^2
+__global__ void k_green_table(double2* table, int nz, int nx, double h, double k) {
+    const int n = (nz + 1) * (nx + 1);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int dx = e / (nz + 1), dz = e - dx * (nz + 1);
+        const double a = h * rsqrt(M_PI);
+        const double ka = k * a;
+        const double pre = M_PI * a / (2.0 * k);        // prefactor is i * pre
+        double2 g;
+        if (dx == 0 && dz == 0) {
+            // i pre (J1 + i Y1) - 1/k^2
+            g = make_double2(-pre * y1(ka) - 1.0 / (k * k), pre * j1(ka));
+        } else {
+            const double kr = k * h * sqrt((double)dz * dz + (double)dx * dx);
+            const double s = pre * j1(ka);
+            // i s (J0 + i Y0)
+            g = make_double2(-s * y0(kr), s * j0(kr));
+        }
+        table[e] = g;
+    }
+}
+
+// even extension of the table to (2bz x 2bx), column-major (2bx columns)
+__global__ void k_extend(const double2* __restrict__ table, int nz, int bz, int bx, double2* ext) {
+    const int pz = 2 * bz, px = 2 * bx;
+    const long long n = (long long)pz * px;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(e / pz), iz = (int)(e - (long long)ix * pz);
+        const int dx = min(ix, px - ix), dz = min(iz, pz - iz);
+        ext[e] = table[dx * (nz + 1) + dz];
+    }
+}
+
+__global__ void k_quarter(const double2* __restrict__ F, int bz, int bx, double2* q64, float2* q32) {
+    const int pz = 2 * bz;
+    const int n = (bz + 1) * (bx + 1);
+    const double sc = 1.0 / (4.0 * bz * bx);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int qx = e / (bz + 1), qz = e - qx * (bz + 1);
+        const double2 v = F[(long long)qx * pz + qz];
+        q64[e] = make_double2(v.x * sc, v.y * sc);
+        q32[e] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+    }
+}
+
+__global__ void k_twiddles(double2* tw64, float2* tw32, int P) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < P; m += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * m / P, &s, &c);
+        tw64[m] = make_double2(c, s);
+        tw32[m] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void k_contrast(const double* __restrict__ vel, double* chi, long long n, double w2, double ic02) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double c = vel[e];
+        chi[e] = w2 * (1.0 / (c * c) - ic02);
+    }
+}
+
+template <typename C>
+__global__ void k_point_sources(const double2* __restrict__ table, int nz, int nx, const int2* __restrict__ pos,
+                                int nsrc, double ih2, C* u0) {
+    const long long n = (long long)nz * nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nsrc; e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / n);
+        const long long i = e - s * n;
+        const int ix = (int)(i / nz), iz = (int)(i - (long long)ix * nz);
+        const int dz = abs(iz - pos[s].x), dx = abs(ix - pos[s].y);
+        const double2 g = table[dx * (nz + 1) + dz];
+        C v;
+        v.x = g.x * ih2;
+        v.y = g.y * ih2;
+        u0[e] = v;
+    }
+}
+
+int grid_for(long long n, int bs = 256) {
+    long long g = (n + bs - 1) / bs;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ op_apply
+template <typename R>
+lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, int mode,
+                    const typename Cx<R>::T* u, const typename Cx<R>::T* u0, typename Cx<R>::T* y,
+                    int nbatch, typename Cx<R>::T* work, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    constexpr int NT = FftCfg<R>::NT, MB4 = FftCfg<R>::MB4, CAP = fft_capacity<R>();
+    if (nbatch <= 0) return LSW_OK;
+    const int bz = geo.bz, bx = geo.bx;
+    const int pz = 2 * bz, px = 2 * bx;
+    if (!is_pow2(bz) || !is_pow2(bx) || pz > CAP || px > CAP) return LSW_ERR_UNSUPPORTED_SIZE;
+    if (sp.bz != bz || sp.bx != bx) return LSW_ERR_INVALID_ARG;
+    const C* tw = reinterpret_cast<const C*>(sizeof(R) == 8 ? (const void*)g->tw64 : (const void*)g->tw32);
+    const C* specq = reinterpret_cast<const C*>(sizeof(R) == 8 ? (const void*)sp.q64 : (const void*)sp.q32);
+
+    DevGeom dg{bz, bx, ilog2(bz), geo.chi, geo.chi_ld, geo.origin, geo.vpb > 0 ? geo.vpb : 1};
+    const int logpz = ilog2(pz), logpx = ilog2(px);
+    // columns per CTA for passes A and C, rows per CTA for pass B
+    int cx = std::min(bx, std::max(1, CAP / pz));
+    cx = std::min(cx, 16);
+    int rz = std::min(pz, std::max(1, CAP / px));
+    rz = std::min(rz, 16);
+    const int lsa = pz + 1, lsb = px + 1;
+    const size_t smA = (size_t)cx * lsa * sizeof(C), smB = (size_t)rz * lsb * sizeof(C);
+    auto ka = k_pass_a<R, NT, MB4>;
+    auto kb = k_pass_b<R, NT, MB4>;
+    auto kc = k_pass_c<R, NT, MB4>;
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[sizeof(R) == 8]) {
+        const int maxsm = 200 * 1024;
+        LSW_CUDA(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        LSW_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        LSW_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+        attr_done[sizeof(R) == 8] = true;
+    }
+    const int twz = g->twP / pz, twx = g->twP / px;
+    dim3 gA(bx / cx, nbatch), gB(pz / rz, nbatch);
+    ka<<<gA, NT, smA, st>>>(u, dg, pz, logpz, cx, ilog2(cx), lsa, tw, twz, mode == LSW_OP_ADJOINT, work);
+    LSW_LAUNCH_CHECK();
+    kb<<<gB, NT, smB, st>>>(work, bx, pz, px, logpx, rz, ilog2(rz), lsb, specq, bz + 1, tw, twx);
+    LSW_LAUNCH_CHECK();
+    kc<<<gA, NT, smA, st>>>(work, dg, pz, logpz, cx, ilog2(cx), lsa, tw, twz, mode, u, u0, y);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template lsw_status op_apply<float>(const lsw_green*, const Spectrum&, const OpGeom&, int, const float2*,
+                                    const float2*, float2*, int, float2*, cudaStream_t);
+template lsw_status op_apply<double>(const lsw_green*, const Spectrum&, const OpGeom&, int, const double2*,
+                                     const double2*, double2*, int, double2*, cudaStream_t);
+
+// ------------------------------------------------------- spectra and table
+lsw_status build_spectrum(const lsw_green* g, int bz, int bx, Spectrum* out, cudaStream_t st) {
+    if (bz > g->nz || bx > g->nx || !is_pow2(bz) || !is_pow2(bx)) return LSW_ERR_INVALID_ARG;
+    const int pz = 2 * bz, px = 2 * bx;
+    constexpr int NT = 256;
+    const int cap = 4 * NT * 4;
+    if (pz > cap || px > cap) return LSW_ERR_UNSUPPORTED_SIZE;
+    DevBuf ext;
+    LSW_TRY(ext.alloc(sizeof(double2) * (size_t)pz * px, st));
+    double2* E = ext.as<double2>();
+    k_extend<<<grid_for((long long)pz * px), 256, 0, st>>>(g->table, g->nz, bz, bx, E);
+    LSW_LAUNCH_CHECK();
+    auto kf = k_fft_strided64<NT>;
+    LSW_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    // along z: px lines of length pz, contiguous
+    {
+        const int lpc = std::max(1, std::min(px, cap / pz));
+        kf<<<(px + lpc - 1) / lpc, NT, sizeof(double2) * lpc * pz, st>>>(E, pz, ilog2(pz), px, lpc, pz, 1,
+                                                                         g->tw64, g->twP / pz, 0);
+        LSW_LAUNCH_CHECK();
+    }
+    // along x: pz lines of length px, stride pz
+    {
+        const int lpc = std::max(1, std::min(pz, cap / px));
+        kf<<<(pz + lpc - 1) / lpc, NT, sizeof(double2) * lpc * px, st>>>(E, px, ilog2(px), pz, lpc, 1, pz,
+                                                                         g->tw64, g->twP / px, 0);
+        LSW_LAUNCH_CHECK();
+    }
+    Spectrum s;
+    s.bz = bz;
+    s.bx = bx;
+    const size_t nq = (size_t)(bz + 1) * (bx + 1);
+    LSW_CUDA(cudaMalloc(&s.q64, nq * sizeof(double2)));
+    if (cudaMalloc(&s.q32, nq * sizeof(float2)) != cudaSuccess) {
+        cudaFree(s.q64);
+        return LSW_ERR_OOM;
+    }
+    k_quarter<<<grid_for((long long)nq), 256, 0, st>>>(E, bz, bx, s.q64, s.q32);
+    LSW_LAUNCH_CHECK();
+    *out = s;
+    return LSW_OK;
+}
+
+void free_spectrum(Spectrum* s) {
+    if (s->q64) cudaFree(s->q64);
+    if (s->q32) cudaFree(s->q32);
+    s->q64 = nullptr;
+    s->q32 = nullptr;
+}
+
+lsw_status green_init(lsw_green* g, cudaStream_t st) {
+    const size_t nt = (size_t)(g->nz + 1) * (g->nx + 1);
+    LSW_CUDA(cudaMalloc(&g->table, nt * sizeof(double2)));
+    k_green_table<<<grid_for((long long)nt), 256, 0, st>>>(g->table, g->nz, g->nx, g->h, g->k);
+    LSW_LAUNCH_CHECK();
+    g->twP = 2 * std::max(g->nz, g->nx);
+    LSW_CUDA(cudaMalloc(&g->tw64, g->twP * sizeof(double2)));
+    LSW_CUDA(cudaMalloc(&g->tw32, g->twP * sizeof(float2)));
+    k_twiddles<<<grid_for(g->twP), 256, 0, st>>>(g->tw64, g->tw32, g->twP);
+    LSW_LAUNCH_CHECK();
+    LSW_TRY(build_spectrum(g, g->nz, g->nx, &g->full, st));
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+lsw_status contrast(const lsw_green* g, const double* vel, double* chi, cudaStream_t st) {
+    const long long n = (long long)g->nz * g->nx;
+    const double w = 2.0 * M_PI * g->freq;
+    k_contrast<<<grid_for(n), 256, 0, st>>>(vel, chi, n, w * w, 1.0 / (g->c0 * g->c0));
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+lsw_status point_sources(const lsw_green* g, const int32_t* pos_host, int nsrc, int prec, void* u0,
+                         cudaStream_t st) {
+    for (int s = 0; s < nsrc; ++s) {
+        if (pos_host[2 * s] < 0 || pos_host[2 * s] >= g->nz || pos_host[2 * s + 1] < 0 ||
+            pos_host[2 * s + 1] >= g->nx)
+            return LSW_ERR_INVALID_ARG;
+    }
+    DevBuf pos;
+    LSW_TRY(pos.alloc(sizeof(int2) * nsrc, st));
+    LSW_CUDA(cudaMemcpyAsync(pos.p, pos_host, sizeof(int2) * nsrc, cudaMemcpyHostToDevice, st));
+    const long long n = (long long)g->nz * g->nx * nsrc;
+    const double ih2 = 1.0 / (g->h * g->h);
+    if (prec == LSW_C128)
+        k_point_sources<double2><<<grid_for(n), 256, 0, st>>>(g->table, g->nz, g->nx, pos.as<int2>(), nsrc, ih2,
+                                                              (double2*)u0);
+    else
+        k_point_sources<float2><<<grid_for(n), 256, 0, st>>>(g->table, g->nz, g->nx, pos.as<int2>(), nsrc, ih2,
+                                                             (float2*)u0);
+    LSW_LAUNCH_CHECK();
+    // the host array is read by an async copy: wait before returning
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+}  // namespace lsw

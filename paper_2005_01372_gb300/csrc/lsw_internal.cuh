@@ -1,0 +1,175 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "lsw.h"
+
+namespace lsw {
+
+// ------------------------------------------------------------ complex types
+template <typename R> struct Cx;
+template <> struct Cx<float>  { typedef float2 T; };
+template <> struct Cx<double> { typedef double2 T; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+    return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// ------------------------------------------------------------------ errors
+#define LSW_CUDA(call)                                             \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) {                                   \
+            lsw::set_last_error(e_, #call, __FILE__, __LINE__);    \
+            return e_ == cudaErrorMemoryAllocation ? LSW_ERR_OOM : LSW_ERR_CUDA; \
+        }                                                          \
+    } while (0)
+#define LSW_TRY(expr)                                              \
+    do {                                                           \
+        lsw_status s_ = (expr);                                    \
+        if (s_ != LSW_OK) return s_;                               \
+    } while (0)
+#define LSW_LAUNCH_CHECK() LSW_CUDA(cudaGetLastError())
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+
+inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
+
+// Stream-ordered scratch that frees itself.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { if (p) cudaFreeAsync(p, s); }
+    lsw_status alloc(size_t bytes, cudaStream_t st) {
+        if (p) { cudaFreeAsync(p, s); p = nullptr; }
+        s = st;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, st);
+        if (e != cudaSuccess) { p = nullptr; set_last_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+                                return e == cudaErrorMemoryAllocation ? LSW_ERR_OOM : LSW_ERR_CUDA; }
+        return LSW_OK;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------ FFT geometry
+// One spectrum of a (bz x bx) box: the FFT of the even extension of the
+// Green table to (2bz x 2bx), scaled by 1/(4 bz bx), as its quarter
+// (bx + 1) x (bz + 1), kx-major.
+struct Spectrum {
+    int bz = 0, bx = 0;
+    double2* q64 = nullptr;
+    float2* q32 = nullptr;
+};
+
+}  // namespace lsw
+
+struct lsw_green {
+    int device;
+    int nz, nx;
+    double h, c0, freq, k;
+    double2* table = nullptr;            // (nx+1) x (nz+1), entry dx*(nz+1)+dz
+    lsw::Spectrum full;                  // spectrum of the whole grid
+    int twP = 0;                         // twiddle table length (max FFT size)
+    double2* tw64 = nullptr;             // tw[m] = exp(-2 pi i m / twP)
+    float2* tw32 = nullptr;
+};
+
+namespace lsw {
+
+// ---------------------------------------------------- operator (fft_op.cu)
+// Geometry of one batched operator launch on boxes of extent (bz, bx):
+// vector b lives at base + b * vstride, its box origin is origin[b / vpb]
+// (NULL: the grid origin), chi is read at chi[(x0 + ix) * chi_ld + z0 + iz].
+struct OpGeom {
+    int bz, bx;
+    const double* chi;
+    int chi_ld;
+    const int2* origin;   // device, may be NULL
+    int vpb;              // vectors per box
+};
+
+template <typename R>
+lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, int mode,
+                    const typename Cx<R>::T* u, const typename Cx<R>::T* u0, typename Cx<R>::T* y,
+                    int nbatch, typename Cx<R>::T* work, cudaStream_t st);
+
+lsw_status build_spectrum(const lsw_green* g, int bz, int bx, Spectrum* out, cudaStream_t st);
+void free_spectrum(Spectrum* s);
+
+// ------------------------------------------------------ dense helpers (la.cu)
+// Batched complex GEMM, column-major:  C_b = alpha * op(A_b) * op(B_b) + beta * C_b
+// op: 'N' or 'C' (conjugate transpose).  A_b = A + b * sA, etc.
+template <typename R>
+lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha,
+                const typename Cx<R>::T* A, int lda, long long sA,
+                const typename Cx<R>::T* B, int ldb, long long sB,
+                typename Cx<R>::T beta, typename Cx<R>::T* C, int ldc, long long sC,
+                int batch, cudaStream_t st);
+
+// Batched thin Householder QR: A_b (m x k, ld m) is replaced by Q_b with
+// orthonormal columns spanning range(A_b) (k <= 64, m >= 1).
+template <typename R>
+lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int batch,
+                       typename Cx<R>::T* work, cudaStream_t st);
+
+// Batched Gram matrices G_b = Y_b^H Y_b (k x k, k <= 64) accumulated in FP64.
+template <typename R>
+lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int batch,
+                  double2* G, cudaStream_t st);
+
+// Batched Hermitian eigen-decomposition by cyclic Jacobi in FP64: G_b (k x k)
+// is replaced by its eigenvectors (columns), sorted by decreasing eigenvalue;
+// lam_b receives the eigenvalues.
+lsw_status heev_jacobi(double2* G, double* lam, int k, int batch, cudaStream_t st);
+
+// Cast FP64 complex -> working precision.
+template <typename R>
+lsw_status cast_from64(const double2* src, typename Cx<R>::T* dst, long long n, cudaStream_t st);
+
+// Philox4x32-10 complex Gaussian probe blocks: block b (m x k, ld m) at
+// dst + b * sD uses stream words w2[b], w3[b] (device arrays).
+template <typename R>
+lsw_status gaussian_fill(typename Cx<R>::T* dst, int m, int k, long long sD, int batch,
+                         uint64_t seed, const uint32_t* w2, const uint32_t* w3, cudaStream_t st);
+
+// Batched in-place inverse of n x n matrices (Gauss-Jordan, partial pivoting).
+template <typename R>
+lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cudaStream_t st);
+
+// Per-field FP64 squared 2-norms: out[b] = sum |x_b|^2 over n entries.
+template <typename R>
+lsw_status norms2(const typename Cx<R>::T* x, long long n, int batch, double* out, cudaStream_t st);
+
+}  // namespace lsw

@@ -1,0 +1,286 @@
+"""Python binding of the lsw C ABI (include/lsw.h): argument marshalling only.
+
+Every computation runs in ``liblsw.so``'s CUDA kernels; this module turns
+torch tensors into device pointers and raises ``LswError`` on a non-zero
+status.  PyTorch supplies device memory and the current CUDA stream.  There is
+no fallback: importing the binding without the built library, or calling it
+without a GPU, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblsw.so")
+
+C128, C64, MIXED = 0, 1, 2
+OP_FORWARD, OP_RESIDUAL, OP_PLAIN, OP_ADJOINT = 0, 1, 2, 3
+H_LOWRANK_SMW, H_HODLR = 0, 1
+SPLIT_QUADTREE, SPLIT_STRIPS = 0, 1
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "OOM", 4: "CUDA",
+          5: "NOT_CONVERGED", 6: "DIVERGED", 7: "NUMERIC", 8: "TIMEOUT"}
+
+
+class LswError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nz", ctypes.c_int32), ("nx", ctypes.c_int32), ("h", ctypes.c_double),
+                ("c0", ctypes.c_double), ("freq_hz", ctypes.c_double)]
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("z0", ctypes.c_int32), ("z1", ctypes.c_int32), ("x0", ctypes.c_int32), ("x1", ctypes.c_int32)]
+
+
+class _HParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("split", ctypes.c_int32), ("rank", ctypes.c_int32), ("oversample", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("pad_", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class _SolveParams(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+
+_lib = None
+VP, I32, U32, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+
+_SIGS = {
+    "lsw_status_string": (ctypes.c_char_p, [I32]),
+    "lsw_last_error": (ctypes.c_char_p, []),
+    "lsw_build_green": (I32, [ctypes.POINTER(_Grid), VP, ctypes.POINTER(VP)]),
+    "lsw_destroy_green": (I32, [VP]),
+    "lsw_green_table": (I32, [VP, VP, VP]),
+    "lsw_green_spectrum": (I32, [VP, VP, VP]),
+    "lsw_contrast": (I32, [VP, VP, VP, VP]),
+    "lsw_point_sources": (I32, [VP, ctypes.POINTER(ctypes.c_int32), I32, I32, VP, VP]),
+    "lsw_apply_operator": (I32, [VP, I32, VP, VP, VP, VP, I32, I32, VP]),
+    "lsw_sketch_range": (I32, [VP, I32, VP, _Box, _Box, I32, I32, I32, U64, U32, VP, VP, VP]),
+    "lsw_build_hmatrix": (I32, [VP, VP, ctypes.POINTER(_HParams), VP, ctypes.POINTER(VP)]),
+    "lsw_destroy_hmatrix": (I32, [VP]),
+    "lsw_hmatrix_bytes": (I32, [VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "lsw_apply_precond": (I32, [VP, VP, VP, I32, VP]),
+    "lsw_solve_series": (I32, [VP, VP, VP, VP, VP, I32, ctypes.POINTER(_SolveParams),
+                               ctypes.POINTER(SolveInfo), VP]),
+}
+
+
+def lib():
+    """The loaded library (loads it on first use; raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2005_01372_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            if not hasattr(L, name):
+                continue          # calling it raises AttributeError
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        detail = ""
+        if st in (3, 4):
+            detail = (lib().lsw_last_error() or b"").decode()
+        raise LswError(st, what, detail)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _cdtype(prec: int):
+    return torch.complex128 if prec in (C128, MIXED) else torch.complex64
+
+
+@dataclass
+class HParams:
+    kind: int = H_HODLR
+    prec: int = C64
+    levels: int = 6
+    split: int = SPLIT_QUADTREE
+    rank: int = 20
+    oversample: int = 10
+    q: int = 0
+    seed: int = 1
+
+    def c(self):
+        return _HParams(self.kind, self.prec, self.levels, self.split, self.rank, self.oversample, self.q, 0,
+                        self.seed)
+
+
+@dataclass
+class SolveParams:
+    prec: int = C128
+    max_iter: int = 30
+    tol: float = 1e-6
+    inner_tol: float = 1e-3
+    max_outer: int = 8
+
+    def c(self):
+        return _SolveParams(self.prec, self.max_iter, self.tol, self.inner_tol, self.max_outer, 0)
+
+
+class Green:
+    """lsw_green handle: Green table and spectra of one (grid, frequency)."""
+
+    def __init__(self, nz: int, nx: int, h: float, c0: float, freq_hz: float, stream=None):
+        self.nz, self.nx, self.h, self.c0, self.freq_hz = nz, nx, h, c0, freq_hz
+        self.n = nz * nx
+        g = _Grid(nz, nx, h, c0, freq_hz)
+        out = VP()
+        _check(lib().lsw_build_green(ctypes.byref(g), _stream(stream), ctypes.byref(out)), "lsw_build_green")
+        self._h = out
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lsw_destroy_green(self._h)
+            self._h = None
+
+    def table(self, stream=None) -> torch.Tensor:
+        t = torch.empty((self.nx + 1, self.nz + 1), dtype=torch.complex128, device="cuda")
+        _check(lib().lsw_green_table(self._h, _ptr(t), _stream(stream)), "lsw_green_table")
+        return t
+
+    def spectrum(self, stream=None) -> torch.Tensor:
+        t = torch.empty((self.nx + 1, self.nz + 1), dtype=torch.complex128, device="cuda")
+        _check(lib().lsw_green_spectrum(self._h, _ptr(t), _stream(stream)), "lsw_green_spectrum")
+        return t
+
+    def contrast(self, velocity: torch.Tensor, stream=None) -> torch.Tensor:
+        chi = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(lib().lsw_contrast(self._h, _ptr(velocity, torch.float64), _ptr(chi), _stream(stream)),
+               "lsw_contrast")
+        return chi
+
+    def point_sources(self, positions, prec: int = C128, stream=None) -> torch.Tensor:
+        pos = (ctypes.c_int32 * (2 * len(positions)))(*[int(v) for p in positions for v in p])
+        u0 = torch.empty((len(positions), self.n), dtype=_cdtype(prec), device="cuda")
+        _check(lib().lsw_point_sources(self._h, pos, len(positions), prec, _ptr(u0), _stream(stream)),
+               "lsw_point_sources")
+        return u0
+
+
+def build_green(nz, nx, h, c0, freq_hz, stream=None) -> Green:
+    return Green(nz, nx, h, c0, freq_hz, stream)
+
+
+def apply_operator(G: Green, chi, u, u0=None, mode: int = OP_PLAIN, y=None, stream=None) -> torch.Tensor:
+    """lsw_apply_operator; u: (nbatch, n) complex128 or complex64."""
+    prec = C128 if u.dtype == torch.complex128 else C64
+    nb = u.numel() // G.n
+    if y is None:
+        y = torch.empty_like(u)
+    _check(lib().lsw_apply_operator(G.handle, prec, _ptr(chi, torch.float64), _ptr(u, u.dtype),
+                                    _ptr(u0, u.dtype) if u0 is not None else None, _ptr(y, u.dtype),
+                                    nb, mode, _stream(stream)), "lsw_apply_operator")
+    return y
+
+
+def sketch_range(G: Green, chi, rows, cols, rank: int, oversample: int, q: int, seed: int, stream_id: int = 0,
+                 prec: int = C128, stream=None):
+    """lsw_sketch_range; rows/cols are (z0, z1, x0, x1).  Returns (U, W),
+    column-major, as tensors of shape (rank, n_rows) and (rank, n_cols)."""
+    ns = (rows[1] - rows[0]) * (rows[3] - rows[2])
+    nt = (cols[1] - cols[0]) * (cols[3] - cols[2])
+    dt = _cdtype(prec)
+    U = torch.empty((rank, ns), dtype=dt, device="cuda")
+    W = torch.empty((rank, nt), dtype=dt, device="cuda")
+    _check(lib().lsw_sketch_range(G.handle, prec, _ptr(chi, torch.float64), _Box(*rows), _Box(*cols), rank,
+                                  oversample, q, seed, stream_id, _ptr(U), _ptr(W), _stream(stream)),
+           "lsw_sketch_range")
+    return U, W
+
+
+class HMatrix:
+    """lsw_hmatrix handle (the preconditioner H)."""
+
+    def __init__(self, G: Green, chi, hp: HParams, stream=None):
+        out = VP()
+        self.prec = hp.prec
+        self.n = G.n
+        c = hp.c()
+        _check(lib().lsw_build_hmatrix(G.handle, _ptr(chi, torch.float64), ctypes.byref(c), _stream(stream),
+                                       ctypes.byref(out)), "lsw_build_hmatrix")
+        self._h = out
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lsw_destroy_hmatrix(self._h)
+            self._h = None
+
+    def nbytes(self) -> int:
+        b = ctypes.c_uint64()
+        _check(lib().lsw_hmatrix_bytes(self._h, ctypes.byref(b)), "lsw_hmatrix_bytes")
+        return b.value
+
+
+def build_hmatrix(G: Green, chi, hp: HParams, stream=None) -> HMatrix:
+    return HMatrix(G, chi, hp, stream)
+
+
+def apply_precond(H: HMatrix, x, y=None, stream=None) -> torch.Tensor:
+    nb = x.numel() // H.n
+    if y is None:
+        y = torch.empty_like(x)
+    _check(lib().lsw_apply_precond(H.handle, _ptr(x, _cdtype(H.prec)), _ptr(y, _cdtype(H.prec)), nb,
+                                   _stream(stream)), "lsw_apply_precond")
+    return y
+
+
+def solve_series(G: Green, chi, H, u0, u=None, sp: SolveParams = None, stream=None, check: bool = False):
+    """lsw_solve_series.  Returns (u, list of SolveInfo).  With check=True a
+    non-converged solve raises; otherwise the status is in the infos."""
+    sp = sp or SolveParams(prec=C128 if u0.dtype == torch.complex128 else C64)
+    nb = u0.numel() // G.n
+    if u is None:
+        u = torch.empty_like(u0)
+    infos = (SolveInfo * nb)()
+    c = sp.c()
+    st = lib().lsw_solve_series(G.handle, _ptr(chi, torch.float64), H.handle if H is not None else None,
+                                _ptr(u0, u0.dtype), _ptr(u, u0.dtype), nb, ctypes.byref(c), infos,
+                                _stream(stream))
+    if st not in (0, 5, 6, 7) or (check and st != 0):
+        _check(st, "lsw_solve_series")
+    return u, list(infos)
