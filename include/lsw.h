@@ -90,12 +90,16 @@ typedef struct {
     uint64_t seed;        /* Philox4x32-10 key of every probe block           */
 } lsw_hparams;
 
+typedef enum { LSW_SERIES = 0, LSW_FGMRES = 1 } lsw_method;
+
 typedef struct {
     int32_t prec;         /* LSW_C128, LSW_C64 or LSW_MIXED                    */
-    int32_t max_iter;     /* series steps per solve (30 in Sec. 3.1)           */
+    int32_t max_iter;     /* series steps (30 in Sec. 3.1) or FGMRES iterations per solve */
     double tol;           /* stop when ||psi0 - (I - G0V) psi||_2 <= tol ||psi0||_2 */
     double inner_tol;     /* LSW_MIXED: relative tolerance of each FP32 inner solve */
     int32_t max_outer;    /* LSW_MIXED: refinement steps                       */
+    int32_t method;       /* lsw_method                                        */
+    int32_t restart;      /* LSW_FGMRES: Krylov basis size per cycle            */
     int32_t pad_;
 } lsw_solve_params;
 
@@ -181,11 +185,16 @@ lsw_status lsw_hmatrix_bytes(const lsw_hmatrix* h, uint64_t* bytes);
  * (hp->prec).  x and y must not alias. */
 lsw_status lsw_apply_precond(const lsw_hmatrix* h, const void* x, void* y, int nbatch, void* stream);
 
-/* Solve (I - G0 V) psi = psi0 for nbatch right-hand sides by the scattering
- * series of Eq. 11, psi_j = psi_{j-1} - H (psi_{j-1} - G0 V psi_{j-1} - psi0),
- * started from psi_0 = H psi0.  H == NULL gives the Born series started from
- * psi0 (Sec. 2.2).  Each source stops once its FP64 relative residual is at
- * most sp->tol (Sec. 3.2 stopping rule, read as relative).
+/* Solve (I - G0 V) psi = psi0 for nbatch right-hand sides.
+ * sp->method LSW_SERIES: the scattering series of Eq. 11,
+ *   psi_j = psi_{j-1} - H (psi_{j-1} - G0 V psi_{j-1} - psi0), started from
+ *   psi_0 = H psi0; H == NULL gives the Born series started from psi0
+ *   (Sec. 2.2).  A source whose residual grows 1e3x above its minimum stops
+ *   with LSW_ERR_DIVERGED (spectral radius of M above one, Eq. 7).
+ * sp->method LSW_FGMRES: flexible GMRES(sp->restart) from psi = 0 with H as
+ *   right preconditioner (H == NULL: none), the Krylov comparison of Sec. 3.2.
+ * Each source stops once its relative residual is at most sp->tol (Sec. 3.2
+ * stopping rule, read as relative); the reported residual is FP64.
  * prec LSW_C128 / LSW_C64: everything in that precision, u0 and u too.
  * prec LSW_MIXED: u0 and u are LSW_C128; iterative refinement -- the FP64
  *   residual r = psi0 - (I - G0 V) psi is formed in FP64, the correction

@@ -1,0 +1,798 @@
+// Preconditioners H ~ (I - G0 V)^-1 (Sec. 2.3-2.4): randomized sketches of
+// blocks of G0 V (Algorithm 2), the simple low-rank + Sherman-Morrison-
+// Woodbury preconditioner (Eq. 12), and the randomized HODLR approximation
+// of I - G0 V with its recursive block inversion (Sec. 2.4, Fig. 1).
+//
+// HODLR storage on the device.  Node (l, c) is node c of level l; every node
+// of a level has n_l = n / 2^l unknowns (power-of-two grids, halving splits),
+// numbered in tree order: leaves left to right, cells of a leaf in strip
+// order.  Block (l, c) -- rows node c, columns its sibling c^1 -- is
+// U_l[c] W_l[c]^H with U_l, W_l arrays of 2^l column-major n_l x r factors;
+// the 2^L dense leaves are D[c], n_L x n_L.  The blocks inside node (l, c)
+// are therefore contiguous ranges of every deeper level's arrays, which turns
+// each operation on a subtree into a few strided batched products.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "lsw_internal.cuh"
+
+namespace lsw {
+
+// ------------------------------------------------------------- cluster tree
+struct Tree {
+    int nz = 0, nx = 0, L = 0, split = 0, n = 0;
+    std::vector<int4> box;           // node (l, c) at (1 << l) - 1 + c: (z0, z1, x0, x1)
+    std::vector<int> perm;           // tree index -> grid index
+    int nl(int l) const { return n >> l; }
+    int4 node(int l, int c) const { return box[(1 << l) - 1 + c]; }
+
+    lsw_status init(int nz_, int nx_, int levels, int split_) {
+        nz = nz_; nx = nx_; L = levels; split = split_; n = nz * nx;
+        box.assign((size_t)(2 << L) - 1, make_int4(0, 0, 0, 0));
+        box[0] = make_int4(0, nz, 0, nx);
+        for (int l = 0; l < L; ++l)
+            for (int c = 0; c < (1 << l); ++c) {
+                const int4 b = node(l, c);
+                const int ez = b.y - b.x, ex = b.w - b.z;
+                const bool along_x = split == LSW_SPLIT_STRIPS || ex >= ez;
+                int4 a = b, d = b;
+                if (along_x) {
+                    if (ex < 2) return LSW_ERR_INVALID_ARG;
+                    const int xm = b.z + ex / 2;
+                    a.w = xm; d.z = xm;
+                } else {
+                    if (ez < 2) return LSW_ERR_INVALID_ARG;
+                    const int zm = b.x + ez / 2;
+                    a.y = zm; d.x = zm;
+                }
+                box[(2 << l) - 1 + 2 * c] = a;
+                box[(2 << l) - 1 + 2 * c + 1] = d;
+            }
+        perm.clear();
+        perm.reserve(n);
+        for (int c = 0; c < (1 << L); ++c) {
+            const int4 b = node(L, c);
+            for (int ix = b.z; ix < b.w; ++ix)
+                for (int iz = b.x; iz < b.y; ++iz) perm.push_back(ix * nz + iz);
+        }
+        return LSW_OK;
+    }
+
+    // position, inside the box of node (l-1, 0), of the unknowns of its child
+    // `which` (tree order); the same for every parent of the level.
+    std::vector<int> child_map(int l, int which) const {
+        const int4 P = node(l - 1, 0);
+        const int pz = P.y - P.x;
+        const int m = nl(l), off = which * m;   // child's first tree index inside parent 0
+        std::vector<int> out(m);
+        for (int i = 0; i < m; ++i) {
+            const int g = perm[off + i];
+            const int ix = g / nz, iz = g % nz;
+            out[i] = (ix - P.z) * pz + (iz - P.x);
+        }
+        return out;
+    }
+};
+
+template <typename R> struct HStore {
+    typedef typename Cx<R>::T C;
+    int L = 0, r = 0, n = 0;
+    C* D = nullptr;
+    std::vector<C*> U, W;   // index by level, [0] unused
+    size_t bytes = 0;
+    int nl(int l) const { return n >> l; }
+    lsw_status alloc(int L_, int r_, int n_) {
+        L = L_; r = r_; n = n_;
+        const int nL = nl(L);
+        const size_t dbytes = sizeof(C) * (size_t)n * nL;
+        if (cudaMalloc(&D, dbytes) != cudaSuccess) return LSW_ERR_OOM;
+        bytes = dbytes;
+        U.assign(L + 1, nullptr);
+        W.assign(L + 1, nullptr);
+        for (int l = 1; l <= L; ++l) {
+            const size_t b = sizeof(C) * (size_t)n * r;   // 2^l blocks x n_l x r
+            if (cudaMalloc(&U[l], b) != cudaSuccess || cudaMalloc(&W[l], b) != cudaSuccess) return LSW_ERR_OOM;
+            bytes += 2 * b;
+        }
+        return LSW_OK;
+    }
+    void release() {
+        if (D) cudaFree(D);
+        for (auto p : U) if (p) cudaFree(p);
+        for (auto p : W) if (p) cudaFree(p);
+        D = nullptr;
+        U.clear();
+        W.clear();
+    }
+};
+
+}  // namespace lsw
+
+struct lsw_hmatrix {
+    int kind = 0, prec = 0, n = 0, r = 0, L = 0, nz = 0, nx = 0;
+    lsw::Tree tree;
+    int* perm_d = nullptr;
+    lsw::HStore<float> h32;
+    lsw::HStore<double> h64;
+    void* smwU = nullptr;    // n x r
+    void* smwW = nullptr;    // n x r
+    void* smwZ = nullptr;    // r x r
+    size_t bytes = 0;
+};
+
+namespace lsw {
+
+namespace {
+
+int gridn(long long n, int bs = 256) {
+    long long g = (n + bs - 1) / bs;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 32));
+}
+
+constexpr uint32_t TAG_BUILD = 1, TAG_GLOBAL = 2, TAG_RECOMPRESS = 3;
+
+uint32_t stream_w2(uint32_t tag, uint32_t op, uint32_t lvl, uint32_t node) {
+    return ((tag & 0xF) << 28) | ((op & 0xF) << 24) | ((lvl & 0xFF) << 16) | (node & 0xFFFF);
+}
+
+// ------------------------------------------------------------- kernels
+// dst vector (b = (c >> 1) * 2rp + (c & 1) * rp + j) at map[which(c)][i]
+//   <- src block c, column j, row i     (which(c) = (c ^ flip) & 1)
+template <typename C>
+__global__ void k_scatter_blocks(const C* __restrict__ src, int nb, int rp, int nblk, const int* __restrict__ map,
+                                 int flip, long long boxn, C* __restrict__ dst) {
+    const long long tot = (long long)nblk * rp * nb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / ((long long)rp * nb));
+        const long long r = e - (long long)c * rp * nb;
+        const int j = (int)(r / nb), i = (int)(r - (long long)j * nb);
+        const int which = (c ^ flip) & 1;
+        const long long b = (long long)(c >> 1) * 2 * rp + (c & 1) * rp + j;
+        dst[b * boxn + map[which * nb + i]] = src[e];
+    }
+}
+
+template <typename C>
+__global__ void k_gather_blocks(const C* __restrict__ src, int nb, int rp, int nblk, const int* __restrict__ map,
+                                int flip, long long boxn, C* __restrict__ dst) {
+    const long long tot = (long long)nblk * rp * nb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / ((long long)rp * nb));
+        const long long r = e - (long long)c * rp * nb;
+        const int j = (int)(r / nb), i = (int)(r - (long long)j * nb);
+        const int which = (c ^ flip) & 1;
+        const long long b = (long long)(c >> 1) * 2 * rp + (c & 1) * rp + j;
+        dst[e] = src[b * boxn + map[which * nb + i]];
+    }
+}
+
+// generic map scatter / gather for one block of k columns
+template <typename C>
+__global__ void k_scatter_map(const C* __restrict__ src, int m, int k, const int* __restrict__ map, long long boxn,
+                              C* __restrict__ dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * k; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / m), i = (int)(e - (long long)j * m);
+        dst[j * boxn + map[i]] = src[e];
+    }
+}
+template <typename C>
+__global__ void k_gather_map(const C* __restrict__ src, int m, int k, const int* __restrict__ map, long long boxn,
+                             C* __restrict__ dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * k; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / m), i = (int)(e - (long long)j * m);
+        dst[e] = src[j * boxn + map[i]];
+    }
+}
+
+// x_tree[s][i] = x_grid[s][perm[i]]   (dir = 0)   or the inverse (dir = 1)
+template <typename C>
+__global__ void k_permute(const C* __restrict__ src, C* __restrict__ dst, const int* __restrict__ perm, int n, int nb,
+                          int dir) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * nb; e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / n), i = (int)(e - (long long)s * n);
+        const long long g = (long long)s * n + perm[i];
+        if (dir == 0) dst[e] = src[g];
+        else dst[g] = src[e];
+    }
+}
+
+// Dense leaf of I - Gt diag(chi): entry (i, j) of leaf c, tree order.
+template <typename C>
+__global__ void k_leaf_assemble(const double2* __restrict__ table, int nz, const double* __restrict__ chi,
+                                const int* __restrict__ perm, int nL, int nleaf, C* __restrict__ D) {
+    const long long per = (long long)nL * nL;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * nleaf; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / per);
+        const long long r = e - (long long)c * per;
+        const int j = (int)(r / nL), i = (int)(r - (long long)j * nL);
+        const int gi = perm[c * nL + i], gj = perm[c * nL + j];
+        const int dz = abs(gi % nz - gj % nz), dx = abs(gi / nz - gj / nz);
+        const double2 g = table[dx * (nz + 1) + dz];
+        const double ch = chi[gj];
+        C v;
+        v.x = (i == j ? 1.0 : 0.0) - g.x * ch;
+        v.y = -g.y * ch;
+        D[e] = v;
+    }
+}
+
+// Uc_b = [U_b | X rows of block b],  Wc_b = [W_b | Y rows of block b ^ 1]
+template <typename C>
+__global__ void k_concat(const C* __restrict__ U, const C* __restrict__ W, const C* __restrict__ X, const C* __restrict__ Y,
+                         int nb, int r, int ldx, int nblk, C* __restrict__ Uc, C* __restrict__ Wc) {
+    const long long per = (long long)nb * 2 * r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * nblk; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / per);
+        const long long q = e - (long long)b * per;
+        const int col = (int)(q / nb), i = (int)(q - (long long)col * nb);
+        if (col < r) {
+            Uc[e] = U[(long long)b * nb * r + (long long)col * nb + i];
+            Wc[e] = W[(long long)b * nb * r + (long long)col * nb + i];
+        } else {
+            const int cc = col - r;
+            Uc[e] = X[(long long)cc * ldx + (long long)b * nb + i];
+            Wc[e] = Y[(long long)cc * ldx + (long long)(b ^ 1) * nb + i];
+        }
+    }
+}
+
+template <typename C>
+__global__ void k_eye_minus(C* M, int r) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+        const int j = e / r, i = e - j * r;
+        C v = M[e];
+        v.x = (i == j ? 1 : 0) - v.x;
+        v.y = -v.y;
+        M[e] = v;
+    }
+}
+
+template <typename C>
+__global__ void k_copy(const C* __restrict__ s, C* __restrict__ d, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) d[e] = s[e];
+}
+
+template <typename C, typename R>
+__global__ void k_scale_copy(const C* __restrict__ s, C* __restrict__ d, long long n, R a) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        C v = s[e];
+        v.x *= a;
+        v.y *= a;
+        d[e] = v;
+    }
+}
+
+template <typename C> C one() { C v; v.x = 1; v.y = 0; return v; }
+template <typename C> C minus_one() { C v; v.x = -1; v.y = 0; return v; }
+template <typename C> C zero() { C v; v.x = 0; v.y = 0; return v; }
+
+template <typename T>
+lsw_status upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    LSW_TRY(b.alloc(sizeof(T) * std::max<size_t>(1, v.size()), st));
+    if (!v.empty()) LSW_CUDA(cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+    return LSW_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- truncation
+// Best rank-r part of Q Yt^H for a batch of blocks (Q: nb x rp, Yt: mb x rp):
+// with Yt^H Yt = V diag(lam) V^H (FP64 Jacobi), keep the r leading
+// eigenvectors Vr:  U = alphaU Q Vr,  W = Yt Vr,  so U W^H = alphaU Q Vr Vr^H Yt^H.
+template <typename R>
+lsw_status truncate(const typename Cx<R>::T* Q, int nb, const typename Cx<R>::T* Yt, int mb, int rp, int r, int nblk,
+                    typename Cx<R>::T alphaU, typename Cx<R>::T* Uout, long long sU, typename Cx<R>::T* Wout,
+                    long long sW, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    DevBuf G, lam, V;
+    LSW_TRY(G.alloc(sizeof(double2) * (size_t)nblk * rp * rp, st));
+    LSW_TRY(lam.alloc(sizeof(double) * (size_t)nblk * rp, st));
+    LSW_TRY(V.alloc(sizeof(C) * (size_t)nblk * rp * rp, st));
+    LSW_TRY(gram64<R>(Yt, mb, rp, (long long)mb * rp, nblk, G.as<double2>(), st));
+    LSW_TRY(heev_jacobi(G.as<double2>(), lam.as<double>(), rp, nblk, st));
+    LSW_TRY(cast_from64<R>(G.as<double2>(), V.as<C>(), (long long)nblk * rp * rp, st));
+    const int rr = std::min(r, rp);
+    if (rr < r) {
+        LSW_CUDA(cudaMemsetAsync(Uout, 0, sizeof(C) * (size_t)sU * nblk, st));
+        LSW_CUDA(cudaMemsetAsync(Wout, 0, sizeof(C) * (size_t)sW * nblk, st));
+    }
+    LSW_TRY(gemm<R>('N', 'N', nb, rr, rp, alphaU, Q, nb, (long long)nb * rp, V.as<C>(), rp, (long long)rp * rp,
+                    zero<C>(), Uout, nb, sU, nblk, st));
+    LSW_TRY(gemm<R>('N', 'N', mb, rr, rp, one<C>(), Yt, mb, (long long)mb * rp, V.as<C>(), rp, (long long)rp * rp,
+                    zero<C>(), Wout, mb, sW, nblk, st));
+    return LSW_OK;
+}
+
+// ---------------------------------------------------------------- sketches
+// Randomized range finder (Algorithm 1/2) for nblk blocks of G0 V on boxes
+// of one shape.  fwd(Xin, Yout): Yout = (G0 V)[s, t] Xin for every block;
+// adj(Xin, Yout): Yout = (G0 V)[s, t]^H Xin.  Q receives the basis
+// (ns x rp per block), Yt the projection (nt x rp).
+template <typename R, typename F, typename A>
+lsw_status range_finder(int ns, int nt, int rp, int q, int nblk, typename Cx<R>::T* Omega, typename Cx<R>::T* Q,
+                        typename Cx<R>::T* Yt, F fwd, A adj, cudaStream_t st) {
+    LSW_TRY(fwd(Omega, Q));
+    LSW_TRY(qr_explicit<R>(Q, ns, rp, (long long)ns * rp, nblk, nullptr, st));
+    for (int it = 0; it < q; ++it) {
+        LSW_TRY(adj(Q, Yt));
+        LSW_TRY(qr_explicit<R>(Yt, nt, rp, (long long)nt * rp, nblk, nullptr, st));
+        LSW_TRY(fwd(Yt, Q));
+        LSW_TRY(qr_explicit<R>(Q, ns, rp, (long long)ns * rp, nblk, nullptr, st));
+    }
+    return adj(Q, Yt);
+}
+
+// One level of the HODLR build: every block (l, c) of I - G0 V is
+// -(G0 V)[node c, node c^1], sketched on the box of the parent node.
+template <typename R>
+lsw_status build_level(const lsw_green* g, const double* chi, const Tree& tr, int l, int r, int rp, int q,
+                       uint64_t seed, HStore<R>& H, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int nblk = 1 << l, npar = 1 << (l - 1), nb = tr.nl(l);
+    const int4 P0 = tr.node(l - 1, 0);
+    const int bz = P0.y - P0.x, bx = P0.w - P0.z;
+    const long long boxn = (long long)bz * bx;
+    Spectrum sp;
+    LSW_TRY(build_spectrum(g, bz, bx, &sp, st));
+    struct SpGuard { Spectrum* s; ~SpGuard() { free_spectrum(s); } } guard{&sp};
+
+    std::vector<int> maps = tr.child_map(l, 0);
+    std::vector<int> m1 = tr.child_map(l, 1);
+    maps.insert(maps.end(), m1.begin(), m1.end());
+    std::vector<int2> org(npar);
+    for (int p = 0; p < npar; ++p) {
+        const int4 b = tr.node(l - 1, p);
+        org[p] = make_int2(b.x, b.z);
+    }
+    std::vector<uint32_t> w2(nblk, stream_w2(TAG_BUILD, 0, 0, 0)), w3(nblk);
+    for (int c = 0; c < nblk; ++c) w3[c] = ((uint32_t)l << 16) | (uint32_t)c;
+    DevBuf dmap, dorg, dw2, dw3, om, qb, yt, vin, vout, work;
+    LSW_TRY(upload(dmap, maps, st));
+    LSW_TRY(upload(dorg, org, st));
+    LSW_TRY(upload(dw2, w2, st));
+    LSW_TRY(upload(dw3, w3, st));
+    const size_t blk = (size_t)nblk * nb * rp;
+    const long long nvec = (long long)npar * 2 * rp;
+    LSW_TRY(om.alloc(sizeof(C) * blk, st));
+    LSW_TRY(qb.alloc(sizeof(C) * blk, st));
+    LSW_TRY(yt.alloc(sizeof(C) * blk, st));
+    LSW_TRY(vin.alloc(sizeof(C) * nvec * boxn, st));
+    LSW_TRY(vout.alloc(sizeof(C) * nvec * boxn, st));
+    LSW_TRY(work.alloc(sizeof(C) * nvec * boxn * 2, st));
+    LSW_TRY(gaussian_fill<R>(om.as<C>(), nb, rp, (long long)nb * rp, nblk, seed, dw2.as<uint32_t>(),
+                             dw3.as<uint32_t>(), st));
+    OpGeom geo{bz, bx, chi, tr.nz, dorg.as<int2>(), 2 * rp};
+    const int* map = dmap.as<int>();
+    // forward: probes on t (= c ^ 1), outputs on s (= c)
+    auto fwd = [&](const C* X, C* Y) -> lsw_status {
+        LSW_CUDA(cudaMemsetAsync(vin.p, 0, sizeof(C) * nvec * boxn, st));
+        k_scatter_blocks<C><<<gridn((long long)blk), 256, 0, st>>>(X, nb, rp, nblk, map, 1, boxn, vin.as<C>());
+        LSW_LAUNCH_CHECK();
+        LSW_TRY(op_apply<R>(g, sp, geo, LSW_OP_PLAIN, vin.as<C>(), nullptr, vout.as<C>(), (int)nvec, work.as<C>(), st));
+        k_gather_blocks<C><<<gridn((long long)blk), 256, 0, st>>>(vout.as<C>(), nb, rp, nblk, map, 0, boxn, Y);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    };
+    auto adj = [&](const C* X, C* Y) -> lsw_status {
+        LSW_CUDA(cudaMemsetAsync(vin.p, 0, sizeof(C) * nvec * boxn, st));
+        k_scatter_blocks<C><<<gridn((long long)blk), 256, 0, st>>>(X, nb, rp, nblk, map, 0, boxn, vin.as<C>());
+        LSW_LAUNCH_CHECK();
+        LSW_TRY(op_apply<R>(g, sp, geo, LSW_OP_ADJOINT, vin.as<C>(), nullptr, vout.as<C>(), (int)nvec, work.as<C>(), st));
+        k_gather_blocks<C><<<gridn((long long)blk), 256, 0, st>>>(vout.as<C>(), nb, rp, nblk, map, 1, boxn, Y);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    };
+    LSW_TRY((range_finder<R>(nb, nb, rp, q, nblk, om.as<C>(), qb.as<C>(), yt.as<C>(), fwd, adj, st)));
+    LSW_TRY(truncate<R>(qb.as<C>(), nb, yt.as<C>(), nb, rp, r, nblk, minus_one<C>(), H.U[l], (long long)nb * r, H.W[l],
+                        (long long)nb * r, st));
+    LSW_CUDA(cudaStreamSynchronize(st));   // the spectrum guard frees on return
+    return LSW_OK;
+}
+
+// ------------------------------------------------------- subtree products
+// Y = X_sub * Xin for node (l, c) (k columns, ld = n_l); T: workspace of
+// 2^(L-l) * r * k complex.
+template <typename R>
+lsw_status hmv(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X, int k, typename Cx<R>::T* Y,
+               typename Cx<R>::T* T, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int m = H.nl(l), L = H.L, r = H.r, nL = H.nl(L);
+    const int nleaf = 1 << (L - l);
+    const C* D0 = H.D + (size_t)c * nleaf * nL * nL;
+    LSW_TRY(gemm<R>('N', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st));
+    for (int lp = l + 1; lp <= L; ++lp) {
+        const int cnt = 1 << (lp - l), nb = H.nl(lp);
+        const size_t first = (size_t)c * cnt;
+        const C* U0 = H.U[lp] + first * nb * r;
+        const C* W0 = H.W[lp] + first * nb * r;
+        // T_j = W_j^H X[sibling rows]
+        LSW_TRY(gemm<R>('C', 'N', r, k, nb, one<C>(), W0, nb, 2LL * nb * r, X + nb, m, 2LL * nb, zero<C>(), T, r,
+                        2LL * r * k, cnt / 2, st));
+        LSW_TRY(gemm<R>('C', 'N', r, k, nb, one<C>(), W0 + (size_t)nb * r, nb, 2LL * nb * r, X, m, 2LL * nb, zero<C>(),
+                        T + (size_t)r * k, r, 2LL * r * k, cnt / 2, st));
+        LSW_TRY(gemm<R>('N', 'N', nb, k, r, one<C>(), U0, nb, (long long)nb * r, T, r, (long long)r * k, one<C>(), Y, m,
+                        nb, cnt, st));
+    }
+    return LSW_OK;
+}
+
+// Y = X_sub^H * Xin for node (l, c).
+template <typename R>
+lsw_status hmv_adj(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X, int k, typename Cx<R>::T* Y,
+                   typename Cx<R>::T* T, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int m = H.nl(l), L = H.L, r = H.r, nL = H.nl(L);
+    const int nleaf = 1 << (L - l);
+    const C* D0 = H.D + (size_t)c * nleaf * nL * nL;
+    LSW_TRY(gemm<R>('C', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st));
+    for (int lp = l + 1; lp <= L; ++lp) {
+        const int cnt = 1 << (lp - l), nb = H.nl(lp);
+        const size_t first = (size_t)c * cnt;
+        const C* U0 = H.U[lp] + first * nb * r;
+        const C* W0 = H.W[lp] + first * nb * r;
+        // T_j = U_j^H X[rows j];  Y[rows j^1] += W_j T_j
+        LSW_TRY(gemm<R>('C', 'N', r, k, nb, one<C>(), U0, nb, (long long)nb * r, X, m, nb, zero<C>(), T, r,
+                        (long long)r * k, cnt, st));
+        LSW_TRY(gemm<R>('N', 'N', nb, k, r, one<C>(), W0, nb, 2LL * nb * r, T, r, 2LL * r * k, one<C>(), Y + nb, m,
+                        2LL * nb, cnt / 2, st));
+        LSW_TRY(gemm<R>('N', 'N', nb, k, r, one<C>(), W0 + (size_t)nb * r, nb, 2LL * nb * r, T + (size_t)r * k, r,
+                        2LL * r * k, one<C>(), Y, m, 2LL * nb, cnt / 2, st));
+    }
+    return LSW_OK;
+}
+
+// Node (l, c) of M += X Y^H (X, Y: n_l x r), every off-diagonal block cut
+// back to rank r by Algorithm 1 (q = 0) through its factors.
+template <typename R>
+lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, const typename Cx<R>::T* Y, int op,
+                       int call_l, int call_c, int oversample, uint64_t seed, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int m = M.nl(l), L = M.L, r = M.r, nL = M.nl(L);
+    const int rp = r + oversample;
+    const int nleaf = 1 << (L - l);
+    C* D0 = M.D + (size_t)c * nleaf * nL * nL;
+    LSW_TRY(gemm<R>('N', 'C', nL, nL, r, one<C>(), X, m, nL, Y, m, nL, one<C>(), D0, nL, (long long)nL * nL, nleaf,
+                    st));
+    for (int lp = l + 1; lp <= L; ++lp) {
+        const int cnt = 1 << (lp - l), nb = M.nl(lp);
+        const size_t first = (size_t)c * cnt;
+        C* U0 = M.U[lp] + first * nb * r;
+        C* W0 = M.W[lp] + first * nb * r;
+        DevBuf uc, wc, om, tt, ys, yt, dw2, dw3;
+        const size_t cat = (size_t)cnt * nb * 2 * r, pro = (size_t)cnt * nb * rp;
+        LSW_TRY(uc.alloc(sizeof(C) * cat, st));
+        LSW_TRY(wc.alloc(sizeof(C) * cat, st));
+        LSW_TRY(om.alloc(sizeof(C) * pro, st));
+        LSW_TRY(ys.alloc(sizeof(C) * pro, st));
+        LSW_TRY(yt.alloc(sizeof(C) * pro, st));
+        LSW_TRY(tt.alloc(sizeof(C) * (size_t)cnt * 2 * r * rp, st));
+        k_concat<C><<<gridn((long long)cat), 256, 0, st>>>(U0, W0, X, Y, nb, r, m, cnt, uc.as<C>(), wc.as<C>());
+        LSW_LAUNCH_CHECK();
+        std::vector<uint32_t> w2(cnt, stream_w2(TAG_RECOMPRESS, op, call_l, call_c)), w3(cnt);
+        for (int j = 0; j < cnt; ++j) w3[j] = ((uint32_t)lp << 16) | (uint32_t)(first + j);
+        LSW_TRY(upload(dw2, w2, st));
+        LSW_TRY(upload(dw3, w3, st));
+        LSW_TRY(gaussian_fill<R>(om.as<C>(), nb, rp, (long long)nb * rp, cnt, seed, dw2.as<uint32_t>(),
+                                 dw3.as<uint32_t>(), st));
+        const long long sc = (long long)nb * 2 * r, sp = (long long)nb * rp, stt = 2LL * r * rp;
+        // Y = Uc (Wc^H Omega)
+        LSW_TRY(gemm<R>('C', 'N', 2 * r, rp, nb, one<C>(), wc.as<C>(), nb, sc, om.as<C>(), nb, sp, zero<C>(), tt.as<C>(),
+                        2 * r, stt, cnt, st));
+        LSW_TRY(gemm<R>('N', 'N', nb, rp, 2 * r, one<C>(), uc.as<C>(), nb, sc, tt.as<C>(), 2 * r, stt, zero<C>(),
+                        ys.as<C>(), nb, sp, cnt, st));
+        LSW_TRY(qr_explicit<R>(ys.as<C>(), nb, rp, sp, cnt, nullptr, st));
+        // Yt = Wc (Uc^H Q)
+        LSW_TRY(gemm<R>('C', 'N', 2 * r, rp, nb, one<C>(), uc.as<C>(), nb, sc, ys.as<C>(), nb, sp, zero<C>(), tt.as<C>(),
+                        2 * r, stt, cnt, st));
+        LSW_TRY(gemm<R>('N', 'N', nb, rp, 2 * r, one<C>(), wc.as<C>(), nb, sc, tt.as<C>(), 2 * r, stt, zero<C>(),
+                        yt.as<C>(), nb, sp, cnt, st));
+        LSW_TRY(truncate<R>(ys.as<C>(), nb, yt.as<C>(), nb, rp, r, cnt, one<C>(), U0, (long long)nb * r, W0,
+                            (long long)nb * r, st));
+    }
+    return LSW_OK;
+}
+
+// Inverse of node (l, c) of X written into the same node of Hi (recursive
+// block inversion).  X's node c+1 subtree is overwritten by the Schur
+// complement S = D - C A^-1 B.
+template <typename R>
+lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample, uint64_t seed, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int L = X.L, r = X.r;
+    if (l == L) {
+        const int nL = X.nl(L);
+        C* d = Hi.D + (size_t)c * nL * nL;
+        k_copy<C><<<gridn((long long)nL * nL), 256, 0, st>>>(X.D + (size_t)c * nL * nL, d, (long long)nL * nL);
+        LSW_LAUNCH_CHECK();
+        return inverse_gj<R>(d, nL, (long long)nL * nL, 1, st);
+    }
+    const int a = 2 * c, b = 2 * c + 1, m1 = X.nl(l + 1);
+    const int nb1 = m1 * r;
+    C* UB = X.U[l + 1] + (size_t)a * nb1;   // B = UB WB^H
+    C* WB = X.W[l + 1] + (size_t)a * nb1;
+    C* UC = X.U[l + 1] + (size_t)b * nb1;   // C = UC WC^H
+    C* WC = X.W[l + 1] + (size_t)b * nb1;
+    LSW_TRY(invert_node<R>(X, l + 1, a, Hi, oversample, seed, st));
+    DevBuf P, Rm, T1, T2, K, XK, T;
+    const size_t vb = sizeof(C) * (size_t)m1 * r;
+    LSW_TRY(P.alloc(vb, st));
+    LSW_TRY(Rm.alloc(vb, st));
+    LSW_TRY(T1.alloc(vb, st));
+    LSW_TRY(T2.alloc(vb, st));
+    LSW_TRY(XK.alloc(vb, st));
+    LSW_TRY(K.alloc(sizeof(C) * r * r, st));
+    LSW_TRY(T.alloc(sizeof(C) * ((size_t)1 << (L - l)) * r * r, st));
+    LSW_TRY(hmv<R>(Hi, l + 1, a, UB, r, P.as<C>(), T.as<C>(), st));        // P = A^-1 UB
+    LSW_TRY(hmv_adj<R>(Hi, l + 1, a, WC, r, Rm.as<C>(), T.as<C>(), st));   // R = A^-H WC
+    LSW_TRY(gemm<R>('C', 'N', r, r, m1, one<C>(), WC, m1, 0, P.as<C>(), m1, 0, zero<C>(), K.as<C>(), r, 0, 1, st));
+    // S = D - UC K WB^H  (in place on X's node b)
+    LSW_TRY(gemm<R>('N', 'N', m1, r, r, minus_one<C>(), UC, m1, 0, K.as<C>(), r, 0, zero<C>(), XK.as<C>(), m1, 0, 1, st));
+    LSW_TRY(add_lowrank<R>(X, l + 1, b, XK.as<C>(), WB, 0, l, c, oversample, seed, st));
+    LSW_TRY(invert_node<R>(X, l + 1, b, Hi, oversample, seed, st));         // S^-1 into Hi
+    LSW_TRY(hmv<R>(Hi, l + 1, b, UC, r, T1.as<C>(), T.as<C>(), st));       // T1 = S^-1 UC
+    LSW_TRY(hmv_adj<R>(Hi, l + 1, b, WB, r, T2.as<C>(), T.as<C>(), st));   // T2 = S^-H WB
+    LSW_TRY(gemm<R>('C', 'N', r, r, m1, one<C>(), WB, m1, 0, T1.as<C>(), m1, 0, zero<C>(), K.as<C>(), r, 0, 1, st));
+    // top-left: A^-1 + P K2 R^H
+    LSW_TRY(gemm<R>('N', 'N', m1, r, r, one<C>(), P.as<C>(), m1, 0, K.as<C>(), r, 0, zero<C>(), XK.as<C>(), m1, 0, 1, st));
+    LSW_TRY(add_lowrank<R>(Hi, l + 1, a, XK.as<C>(), Rm.as<C>(), 1, l, c, oversample, seed, st));
+    // off-diagonal blocks of the inverse: -P T2^H and -T1 R^H
+    const long long nn = (long long)m1 * r;
+    k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(P.as<C>(), Hi.U[l + 1] + (size_t)a * nb1, nn, (R)-1);
+    k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(T2.as<C>(), Hi.W[l + 1] + (size_t)a * nb1, nn, (R)1);
+    k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(T1.as<C>(), Hi.U[l + 1] + (size_t)b * nb1, nn, (R)-1);
+    k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(Rm.as<C>(), Hi.W[l + 1] + (size_t)b * nb1, nn, (R)1);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+// ------------------------------------------------------------ full builds
+template <typename R>
+lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams* hp, lsw_hmatrix* h, cudaStream_t st,
+                       HStore<R>& Hi) {
+    typedef typename Cx<R>::T C;
+    const Tree& tr = h->tree;
+    const int L = hp->levels, r = hp->rank, rp = hp->rank + hp->oversample;
+    HStore<R> X;
+    struct Rel { HStore<R>* s; ~Rel() { s->release(); } } rel{&X};
+    LSW_TRY(X.alloc(L, r, tr.n));
+    for (int l = 1; l <= L; ++l) LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, st));
+    const int nL = tr.nl(L);
+    k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, st>>>(g->table, g->nz, chi, h->perm_d, nL, 1 << L, X.D);
+    LSW_LAUNCH_CHECK();
+    LSW_TRY(Hi.alloc(L, r, tr.n));
+    LSW_TRY(invert_node<R>(X, 0, 0, Hi, hp->oversample, hp->seed, st));
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+// Sketch (G0 V)[s, t] ~ U W^H for boxes s, t inside the grid (strip order
+// inside each box).  alphaU scales U.
+template <typename R>
+lsw_status sketch_boxes(const lsw_green* g, const double* chi, lsw_box s, lsw_box t, int r, int oversample, int q,
+                        uint64_t seed, uint32_t w2v, uint32_t w3v, typename Cx<R>::T alphaU, typename Cx<R>::T* U,
+                        typename Cx<R>::T* W, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int rp = r + oversample;
+    lsw_box B{std::min(s.z0, t.z0), std::max(s.z1, t.z1), std::min(s.x0, t.x0), std::max(s.x1, t.x1)};
+    if (!is_pow2(B.z1 - B.z0) || !is_pow2(B.x1 - B.x0)) B = lsw_box{0, g->nz, 0, g->nx};
+    const int bz = B.z1 - B.z0, bx = B.x1 - B.x0;
+    const long long boxn = (long long)bz * bx;
+    const int ns = (s.z1 - s.z0) * (s.x1 - s.x0), nt = (t.z1 - t.z0) * (t.x1 - t.x0);
+    auto mapof = [&](lsw_box q_) {
+        std::vector<int> m;
+        for (int ix = q_.x0; ix < q_.x1; ++ix)
+            for (int iz = q_.z0; iz < q_.z1; ++iz) m.push_back((ix - B.x0) * bz + (iz - B.z0));
+        return m;
+    };
+    Spectrum sp;
+    const bool full = (bz == g->nz && bx == g->nx);
+    if (!full) LSW_TRY(build_spectrum(g, bz, bx, &sp, st));
+    struct SpGuard { Spectrum* s; bool own; ~SpGuard() { if (own) free_spectrum(s); } } guard{&sp, !full};
+    const Spectrum& spec = full ? g->full : sp;
+    DevBuf ms, mt, dorg, dw2, dw3, om, qb, yt, vin, vout, work;
+    LSW_TRY(upload(ms, mapof(s), st));
+    LSW_TRY(upload(mt, mapof(t), st));
+    LSW_TRY(upload(dorg, std::vector<int2>{make_int2(B.z0, B.x0)}, st));
+    LSW_TRY(upload(dw2, std::vector<uint32_t>{w2v}, st));
+    LSW_TRY(upload(dw3, std::vector<uint32_t>{w3v}, st));
+    LSW_TRY(om.alloc(sizeof(C) * (size_t)nt * rp, st));
+    LSW_TRY(qb.alloc(sizeof(C) * (size_t)ns * rp, st));
+    LSW_TRY(yt.alloc(sizeof(C) * (size_t)nt * rp, st));
+    LSW_TRY(vin.alloc(sizeof(C) * rp * boxn, st));
+    LSW_TRY(vout.alloc(sizeof(C) * rp * boxn, st));
+    LSW_TRY(work.alloc(sizeof(C) * rp * boxn * 2, st));
+    LSW_TRY(gaussian_fill<R>(om.as<C>(), nt, rp, (long long)nt * rp, 1, seed, dw2.as<uint32_t>(), dw3.as<uint32_t>(), st));
+    OpGeom geo{bz, bx, chi, g->nz, dorg.as<int2>(), rp};
+    auto fwd = [&](const C* X, C* Y) -> lsw_status {
+        LSW_CUDA(cudaMemsetAsync(vin.p, 0, sizeof(C) * rp * boxn, st));
+        k_scatter_map<C><<<gridn((long long)nt * rp), 256, 0, st>>>(X, nt, rp, mt.as<int>(), boxn, vin.as<C>());
+        LSW_LAUNCH_CHECK();
+        LSW_TRY(op_apply<R>(g, spec, geo, LSW_OP_PLAIN, vin.as<C>(), nullptr, vout.as<C>(), rp, work.as<C>(), st));
+        k_gather_map<C><<<gridn((long long)ns * rp), 256, 0, st>>>(vout.as<C>(), ns, rp, ms.as<int>(), boxn, Y);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    };
+    auto adj = [&](const C* X, C* Y) -> lsw_status {
+        LSW_CUDA(cudaMemsetAsync(vin.p, 0, sizeof(C) * rp * boxn, st));
+        k_scatter_map<C><<<gridn((long long)ns * rp), 256, 0, st>>>(X, ns, rp, ms.as<int>(), boxn, vin.as<C>());
+        LSW_LAUNCH_CHECK();
+        LSW_TRY(op_apply<R>(g, spec, geo, LSW_OP_ADJOINT, vin.as<C>(), nullptr, vout.as<C>(), rp, work.as<C>(), st));
+        k_gather_map<C><<<gridn((long long)nt * rp), 256, 0, st>>>(vout.as<C>(), nt, rp, mt.as<int>(), boxn, Y);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    };
+    LSW_TRY((range_finder<R>(ns, nt, rp, q, 1, om.as<C>(), qb.as<C>(), yt.as<C>(), fwd, adj, st)));
+    LSW_TRY(truncate<R>(qb.as<C>(), ns, yt.as<C>(), nt, rp, r, 1, alphaU, U, (long long)ns * r, W, (long long)nt * r, st));
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status build_smw(const lsw_green* g, const double* chi, const lsw_hparams* hp, lsw_hmatrix* h, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int n = h->n, r = hp->rank;
+    LSW_CUDA(cudaMalloc(&h->smwU, sizeof(C) * (size_t)n * r));
+    LSW_CUDA(cudaMalloc(&h->smwW, sizeof(C) * (size_t)n * r));
+    LSW_CUDA(cudaMalloc(&h->smwZ, sizeof(C) * (size_t)r * r));
+    h->bytes = sizeof(C) * ((size_t)2 * n * r + (size_t)r * r);
+    C* U = (C*)h->smwU;
+    C* W = (C*)h->smwW;
+    C* Z = (C*)h->smwZ;
+    lsw_box all{0, g->nz, 0, g->nx};
+    LSW_TRY(sketch_boxes<R>(g, chi, all, all, r, hp->oversample, hp->q, hp->seed, stream_w2(TAG_GLOBAL, 0, 0, 0), 0,
+                            one<C>(), U, W, st));
+    // Z = (I_r - W^H U)^-1   (Eq. 12)
+    LSW_TRY(gemm<R>('C', 'N', r, r, n, one<C>(), W, n, 0, U, n, 0, zero<C>(), Z, r, 0, 1, st));
+    k_eye_minus<C><<<1, 256, 0, st>>>(Z, r);
+    LSW_LAUNCH_CHECK();
+    LSW_TRY(inverse_gj<R>(Z, r, (long long)r * r, 1, st));
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+// y = H x (grid order, nb fields)
+template <typename R>
+lsw_status apply_h(const lsw_hmatrix* h, const typename Cx<R>::T* x, typename Cx<R>::T* y, int nb, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int n = h->n, r = h->r;
+    if (nb <= 0) return LSW_OK;
+    if (h->kind == LSW_H_LOWRANK_SMW) {
+        const C* U = (const C*)h->smwU;
+        const C* W = (const C*)h->smwW;
+        const C* Z = (const C*)h->smwZ;
+        DevBuf t1, t2;
+        LSW_TRY(t1.alloc(sizeof(C) * (size_t)r * nb, st));
+        LSW_TRY(t2.alloc(sizeof(C) * (size_t)r * nb, st));
+        // y = x + U (Z (W^H x))   (Eq. 12 applied as three factors, Eq. 14)
+        LSW_TRY(gemm<R>('C', 'N', r, nb, n, one<C>(), W, n, 0, x, n, 0, zero<C>(), t1.as<C>(), r, 0, 1, st));
+        LSW_TRY(gemm<R>('N', 'N', r, nb, r, one<C>(), Z, r, 0, t1.as<C>(), r, 0, zero<C>(), t2.as<C>(), r, 0, 1, st));
+        LSW_CUDA(cudaMemcpyAsync(y, x, sizeof(C) * (size_t)n * nb, cudaMemcpyDeviceToDevice, st));
+        LSW_TRY(gemm<R>('N', 'N', n, nb, r, one<C>(), U, n, 0, t2.as<C>(), r, 0, one<C>(), y, n, 0, 1, st));
+        return LSW_OK;
+    }
+    const HStore<R>& H = *reinterpret_cast<const HStore<R>*>(sizeof(R) == 8 ? (const void*)&h->h64 : (const void*)&h->h32);
+    DevBuf xt, yt, T;
+    LSW_TRY(xt.alloc(sizeof(C) * (size_t)n * nb, st));
+    LSW_TRY(yt.alloc(sizeof(C) * (size_t)n * nb, st));
+    LSW_TRY(T.alloc(sizeof(C) * ((size_t)1 << h->L) * r * nb, st));
+    k_permute<C><<<gridn((long long)n * nb), 256, 0, st>>>(x, xt.as<C>(), h->perm_d, n, nb, 0);
+    LSW_LAUNCH_CHECK();
+    LSW_TRY(hmv<R>(H, 0, 0, xt.as<C>(), nb, yt.as<C>(), T.as<C>(), st));
+    k_permute<C><<<gridn((long long)n * nb), 256, 0, st>>>(yt.as<C>(), y, h->perm_d, n, nb, 1);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+int hmatrix_prec(const lsw_hmatrix* h) { return h->prec; }
+
+template lsw_status apply_h<float>(const lsw_hmatrix*, const float2*, float2*, int, cudaStream_t);
+template lsw_status apply_h<double>(const lsw_hmatrix*, const double2*, double2*, int, cudaStream_t);
+
+}  // namespace lsw
+
+using namespace lsw;
+
+extern "C" {
+
+lsw_status lsw_sketch_range(const lsw_green* g, int prec, const double* chi, lsw_box rows, lsw_box cols, int rank,
+                            int oversample, int q, uint64_t seed, uint32_t stream_id, void* U, void* W, void* stream) {
+    if (!g || !chi || !U || !W || rank <= 0 || oversample < 0 || q < 0) return LSW_ERR_INVALID_ARG;
+    if (rank + oversample > 64) return LSW_ERR_INVALID_ARG;
+    auto inside = [&](lsw_box b) {
+        return b.z0 >= 0 && b.z1 <= g->nz && b.x0 >= 0 && b.x1 <= g->nx && b.z0 < b.z1 && b.x0 < b.x1;
+    };
+    if (!inside(rows) || !inside(cols)) return LSW_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint32_t w2 = stream_w2(TAG_GLOBAL, 0, 0, 0);
+    if (prec == LSW_C128)
+        return sketch_boxes<double>(g, chi, rows, cols, rank, oversample, q, seed, w2, stream_id, one<double2>(),
+                                    (double2*)U, (double2*)W, st);
+    if (prec == LSW_C64)
+        return sketch_boxes<float>(g, chi, rows, cols, rank, oversample, q, seed, w2, stream_id, one<float2>(),
+                                   (float2*)U, (float2*)W, st);
+    return LSW_ERR_INVALID_ARG;
+}
+
+lsw_status lsw_build_hmatrix(const lsw_green* g, const double* chi, const lsw_hparams* hp, void* stream,
+                             lsw_hmatrix** out) {
+    if (!g || !chi || !hp || !out) return LSW_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (hp->prec != LSW_C128 && hp->prec != LSW_C64) return LSW_ERR_INVALID_ARG;
+    if (hp->rank <= 0 || hp->oversample < 0 || hp->q < 0 || hp->rank + hp->oversample > 64) return LSW_ERR_INVALID_ARG;
+    if (hp->kind != LSW_H_LOWRANK_SMW && hp->kind != LSW_H_HODLR) return LSW_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    lsw_hmatrix* h = new (std::nothrow) lsw_hmatrix();
+    if (!h) return LSW_ERR_OOM;
+    h->kind = hp->kind;
+    h->prec = hp->prec;
+    h->n = g->nz * g->nx;
+    h->nz = g->nz;
+    h->nx = g->nx;
+    h->r = hp->rank;
+    lsw_status s = LSW_OK;
+    if (hp->kind == LSW_H_LOWRANK_SMW) {
+        s = hp->prec == LSW_C128 ? build_smw<double>(g, chi, hp, h, st) : build_smw<float>(g, chi, hp, h, st);
+    } else {
+        if (hp->levels < 1 || hp->levels > 12 || (hp->split != LSW_SPLIT_QUADTREE && hp->split != LSW_SPLIT_STRIPS)) {
+            delete h;
+            return LSW_ERR_INVALID_ARG;
+        }
+        h->L = hp->levels;
+        s = h->tree.init(g->nz, g->nx, hp->levels, hp->split);
+        if (s == LSW_OK) {
+            const size_t pb = sizeof(int) * h->tree.perm.size();
+            if (cudaMalloc(&h->perm_d, pb) != cudaSuccess) s = LSW_ERR_OOM;
+            else if (cudaMemcpy(h->perm_d, h->tree.perm.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess) s = LSW_ERR_CUDA;
+        }
+        if (s == LSW_OK) {
+            if (hp->prec == LSW_C128) {
+                s = build_hodlr<double>(g, chi, hp, h, st, h->h64);
+                h->bytes = h->h64.bytes;
+            } else {
+                s = build_hodlr<float>(g, chi, hp, h, st, h->h32);
+                h->bytes = h->h32.bytes;
+            }
+        }
+    }
+    if (s != LSW_OK) {
+        lsw_destroy_hmatrix(h);
+        return s;
+    }
+    *out = h;
+    return LSW_OK;
+}
+
+lsw_status lsw_destroy_hmatrix(lsw_hmatrix* h) {
+    if (!h) return LSW_ERR_INVALID_ARG;
+    h->h32.release();
+    h->h64.release();
+    if (h->perm_d) cudaFree(h->perm_d);
+    if (h->smwU) cudaFree(h->smwU);
+    if (h->smwW) cudaFree(h->smwW);
+    if (h->smwZ) cudaFree(h->smwZ);
+    delete h;
+    return LSW_OK;
+}
+
+lsw_status lsw_hmatrix_bytes(const lsw_hmatrix* h, uint64_t* bytes) {
+    if (!h || !bytes) return LSW_ERR_INVALID_ARG;
+    *bytes = h->bytes + sizeof(int) * (size_t)h->n * (h->perm_d ? 1 : 0);
+    return LSW_OK;
+}
+
+lsw_status lsw_apply_precond(const lsw_hmatrix* h, const void* x, void* y, int nbatch, void* stream) {
+    if (!h || nbatch < 0) return LSW_ERR_INVALID_ARG;
+    if (nbatch == 0) return LSW_OK;
+    if (!x || !y || x == y) return LSW_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (h->prec == LSW_C128) return apply_h<double>(h, (const double2*)x, (double2*)y, nbatch, st);
+    return apply_h<float>(h, (const float2*)x, (float2*)y, nbatch, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,850 @@
+// Dense kernels of the preconditioner build and apply: batched complex GEMM,
+// thin Householder QR, FP64 Gram matrices, Jacobi eigen-decomposition of
+// small Hermitian matrices, Philox Gaussian probes, blocked Gauss-Jordan
+// inversion, norms.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "lsw_internal.cuh"
+
+namespace lsw {
+
+namespace {
+
+int grid_for(long long n, int bs = 256) {
+    long long g = (n + bs - 1) / bs;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 32));
+}
+
+template <typename C> __device__ __forceinline__ C ldop(const C* p, bool conj_) {
+    C v = *p;
+    if (conj_) v.y = -v.y;
+    return v;
+}
+
+// ------------------------------------------------------------------ GEMM
+// 64 x 64 output tile per CTA, 256 threads, 4 x 4 complex outputs per
+// thread, K in steps of 8.  blockIdx.z = batch * ksplit + kpart; with
+// ksplit > 1 the partial products go to P (ksplit x batch x m x n) and a
+// second kernel reduces them in a fixed order.
+constexpr int GBM = 64, GBN = 64, GBK = 8;
+
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, int lda, long long sA,
+       const C* __restrict__ B, int ldb, long long sB, C beta, C* __restrict__ Cm, int ldc, long long sC,
+       int ksplit, int kchunk, C* __restrict__ P) {
+    __shared__ C As[GBK][GBM + 1];
+    __shared__ C Bs[GBK][GBN + 1];
+    const int bz = blockIdx.z;
+    const int b = bz / ksplit, kp = bz - b * ksplit;
+    const int i0 = blockIdx.x * GBM, j0 = blockIdx.y * GBN;
+    const int kbeg = kp * kchunk, kend = min(k, kbeg + kchunk);
+    const C* Ab = A + b * sA;
+    const C* Bb = B + b * sB;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = czero<C>();
+    for (int kk = kbeg; kk < kend; kk += GBK) {
+        // A tile: GBM x GBK  (element (i, kk+t))
+        for (int e = threadIdx.x; e < GBM * GBK; e += 256) {
+            int i, t;
+            if (opA == 0) { i = e % GBM; t = e / GBM; } else { t = e % GBK; i = e / GBK; }
+            const int gi = i0 + i, gk = kk + t;
+            C v = czero<C>();
+            if (gi < m && gk < kend) v = opA == 0 ? Ab[(long long)gk * lda + gi] : ldop(Ab + (long long)gi * lda + gk, true);
+            As[t][i] = v;
+        }
+        // B tile: GBK x GBN  (element (kk+t, j))
+        for (int e = threadIdx.x; e < GBK * GBN; e += 256) {
+            int t, j;
+            if (opB == 0) { t = e % GBK; j = e / GBK; } else { j = e % GBN; t = e / GBN; }
+            const int gj = j0 + j, gk = kk + t;
+            C v = czero<C>();
+            if (gj < n && gk < kend) v = opB == 0 ? Bb[(long long)gj * ldb + gk] : ldop(Bb + (long long)gk * ldb + gj, true);
+            Bs[t][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < GBK; ++t) {
+            C a[4], bb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = As[t][ty + 16 * q]; bb[q] = Bs[t][tx + 16 * q]; }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cfma(acc[p][q], a[p], bb[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+            if (gi < m && gj < n) {
+                if (ksplit == 1) {
+                    C* c = Cm + b * sC + (long long)gj * ldc + gi;
+                    C r = cmul(alpha, acc[p][q]);
+                    if (beta.x != 0 || beta.y != 0) r = cadd(r, cmul(beta, *c));
+                    *c = r;
+                } else {
+                    P[(((long long)kp * gridDim.z / ksplit + b) * n + gj) * m + gi] = acc[p][q];
+                }
+            }
+        }
+}
+
+template <typename C>
+__global__ void k_gemm_reduce(int m, int n, int batch, int ksplit, const C* __restrict__ P, C alpha, C beta,
+                              C* __restrict__ Cm, int ldc, long long sC) {
+    const long long tot = (long long)batch * m * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / ((long long)m * n));
+        const long long r = e - (long long)b * m * n;
+        const int j = (int)(r / m), i = (int)(r - (long long)j * m);
+        C s = czero<C>();
+        for (int kp = 0; kp < ksplit; ++kp) s = cadd(s, P[(((long long)kp * batch + b) * n + j) * m + i]);
+        C* c = Cm + b * sC + (long long)j * ldc + i;
+        C out = cmul(alpha, s);
+        if (beta.x != 0 || beta.y != 0) out = cadd(out, cmul(beta, *c));
+        *c = out;
+    }
+}
+
+// ------------------------------------------------------------ FP64 Gram
+// G_b = Y_b^H Y_b, k x k (k <= 64), partial sums over row chunks; each
+// thread owns up to 16 of the k^2 entries.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_gram_partial(const C* __restrict__ Y, int m, int k, long long sY, int nchunk, double2* __restrict__ part) {
+    constexpr int TR = 32, MAXQ = 16;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* sy = reinterpret_cast<C*>(sm_raw);      // TR rows x k
+    const int b = blockIdx.y, ch = blockIdx.x;
+    const int rows_per = (m + nchunk - 1) / nchunk;
+    const int r0 = ch * rows_per, r1 = min(m, r0 + rows_per);
+    const C* Yb = Y + b * sY;
+    const int npair = k * k;
+    double2 acc[MAXQ];
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) acc[q] = make_double2(0, 0);
+    for (int rr = r0; rr < r1; rr += TR) {
+        const int nr = min(TR, r1 - rr);
+        for (int e = threadIdx.x; e < TR * k; e += 256) {
+            const int c = e / TR, r = e % TR;
+            sy[c * TR + r] = r < nr ? Yb[(long long)c * m + rr + r] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q) {
+            const int pidx = threadIdx.x + q * 256;
+            if (pidx < npair) {
+                const int i = pidx % k, j = pidx / k;
+                const C* yi = sy + i * TR;
+                const C* yj = sy + j * TR;
+                double sx = acc[q].x, syy = acc[q].y;
+                for (int r = 0; r < nr; ++r) {
+                    const double ax = yi[r].x, ay = yi[r].y, bx = yj[r].x, by = yj[r].y;
+                    sx += ax * bx + ay * by;
+                    syy += ax * by - ay * bx;
+                }
+                acc[q] = make_double2(sx, syy);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+        const int pidx = threadIdx.x + q * 256;
+        if (pidx < npair) part[((long long)b * nchunk + ch) * npair + pidx] = acc[q];
+    }
+}
+
+__global__ void k_gram_reduce(const double2* __restrict__ part, int nchunk, int npair, int batch, double2* G) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < batch * npair; e += gridDim.x * blockDim.x) {
+        const int b = e / npair, p = e - b * npair;
+        double2 s = make_double2(0, 0);
+        for (int c = 0; c < nchunk; ++c) {
+            const double2 v = part[((long long)b * nchunk + c) * npair + p];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        G[e] = s;
+    }
+}
+
+// ------------------------------------------------- Householder QR (thin)
+// One CTA per matrix.  Reflectors follow LAPACK's zlarfg convention:
+// H = I - tau v v^H with v(0) = 1, H^H [alpha; x] = [beta; 0], beta real.
+template <typename C, int NT>
+__device__ __forceinline__ C block_sum(C v, C* red) {
+    typedef decltype(v.x) R;
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    C s = czero<C>();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < NT / 32 ? red[threadIdx.x] : czero<C>();
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (threadIdx.x == 0) red[32] = s;
+    }
+    __syncthreads();
+    s = red[32];
+    (void)sizeof(R);
+    return s;
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT)
+k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA) {
+    typedef typename Cx<R>::T C;
+    __shared__ C red[33];
+    __shared__ C tau_s[64];
+    __shared__ C wv[16];
+    C* A = Aall + blockIdx.x * sA;
+    const int kk = min(k, m);
+    // ---- factorisation
+    for (int j = 0; j < kk; ++j) {
+        C* aj = A + (long long)j * m;
+        C part = czero<C>();
+        for (int i = j + 1 + threadIdx.x; i < m; i += NT) part.x += aj[i].x * aj[i].x + aj[i].y * aj[i].y;
+        const R xnorm2 = block_sum<C, NT>(part, red).x;
+        const C alpha = aj[j];
+        C tau = czero<C>();
+        R beta = alpha.x;
+        bool skip = (xnorm2 == 0 && alpha.y == 0);
+        if (!skip) {
+            const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+            beta = alpha.x >= 0 ? -nrm : nrm;
+            tau = mk((beta - alpha.x) / beta, -alpha.y / beta);
+            // scale = 1 / (alpha - beta)
+            const C d = mk(alpha.x - beta, alpha.y);
+            const R den = d.x * d.x + d.y * d.y;
+            const C sc = mk(d.x / den, -d.y / den);
+            for (int i = j + 1 + threadIdx.x; i < m; i += NT) aj[i] = cmul(aj[i], sc);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tau_s[j] = tau;
+            aj[j] = mk(beta, (R)0);
+        }
+        __syncthreads();
+        if (skip) continue;
+        // apply H^H = I - conj(tau) v v^H to columns j+1..k-1, 16 at a time
+        for (int c0 = j + 1; c0 < k; c0 += 16) {
+            const int nc = min(16, k - c0);
+            C acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
+            for (int i = j + threadIdx.x; i < m; i += NT) {
+                const C v = i == j ? mk((R)1, (R)0) : aj[i];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (q < nc) cfmac(acc[q], v, A[(long long)(c0 + q) * m + i]);
+            }
+            for (int q = 0; q < nc; ++q) {
+                C s = block_sum<C, NT>(acc[q], red);
+                if (threadIdx.x == 0) wv[q] = cmulc(tau, s);   // conj(tau) * (v^H a)
+            }
+            __syncthreads();
+            for (int i = j + threadIdx.x; i < m; i += NT) {
+                const C v = i == j ? mk((R)1, (R)0) : aj[i];
+                for (int q = 0; q < nc; ++q) {
+                    C* a = A + (long long)(c0 + q) * m + i;
+                    *a = csub(*a, cmul(v, wv[q]));
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- explicit Q = H_0 H_1 ... H_{k-1} [I; 0]
+    for (int j = k - 1; j >= 0; --j) {
+        C* aj = A + (long long)j * m;
+        if (j >= kk) {
+            // more columns than rows: column j of Q is zero
+            for (int i = threadIdx.x; i < m; i += NT) aj[i] = czero<C>();
+            __syncthreads();
+            continue;
+        }
+        const C tau = tau_s[j];
+        for (int c0 = j + 1; c0 < k; c0 += 16) {
+            const int nc = min(16, k - c0);
+            C acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
+            for (int i = j + threadIdx.x; i < m; i += NT) {
+                const C v = i == j ? mk((R)1, (R)0) : aj[i];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (q < nc) cfmac(acc[q], v, A[(long long)(c0 + q) * m + i]);
+            }
+            for (int q = 0; q < nc; ++q) {
+                C s = block_sum<C, NT>(acc[q], red);
+                if (threadIdx.x == 0) wv[q] = cmul(tau, s);      // tau * (v^H a)
+            }
+            __syncthreads();
+            for (int i = j + threadIdx.x; i < m; i += NT) {
+                const C v = i == j ? mk((R)1, (R)0) : aj[i];
+                for (int q = 0; q < nc; ++q) {
+                    C* a = A + (long long)(c0 + q) * m + i;
+                    *a = csub(*a, cmul(v, wv[q]));
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < m; i += NT) {
+            if (i < j) aj[i] = czero<C>();
+            else if (i == j) aj[i] = mk((R)1 - tau.x, -tau.y);
+            else aj[i] = mk(-(tau.x * aj[i].x - tau.y * aj[i].y), -(tau.x * aj[i].y + tau.y * aj[i].x));
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------- Jacobi eigen (Hermitian)
+// Parallel cyclic Jacobi: each round rotates k/2 disjoint index pairs chosen
+// by the circle method, so every pair is met once per sweep.
+__global__ void __launch_bounds__(256) k_heev_jacobi(double2* __restrict__ Gall, double* __restrict__ lam_all, int k) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int m = (k + 1) & ~1;                 // even number of players
+    double2* A = reinterpret_cast<double2*>(sm_raw);   // k x k, column-major
+    double2* V = A + k * k;
+    double4* rot = reinterpret_cast<double4*>(V + k * k);   // per pair: cs, sn, cos(phi), sin(phi)
+    int2* pr = reinterpret_cast<int2*>(rot + m / 2);
+    __shared__ double offn, totn;
+    double2* G = Gall + (long long)blockIdx.x * k * k;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        A[e] = G[e];
+        V[e] = make_double2((e % k) == (e / k) ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (threadIdx.x == 0) {
+            double o = 0, t = 0;
+            for (int j = 0; j < k; ++j)
+                for (int i = 0; i < k; ++i) {
+                    const double2 a = A[j * k + i];
+                    const double v = a.x * a.x + a.y * a.y;
+                    t += v;
+                    if (i != j) o += v;
+                }
+            offn = o;
+            totn = t;
+        }
+        __syncthreads();
+        if (!(offn > 1e-30 * totn) || totn == 0) break;
+        for (int r = 0; r < m - 1; ++r) {
+            // pairs of this round
+            for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
+                int p, q;
+                if (i == 0) { p = m - 1; q = r; }
+                else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
+                if (p > q) { const int t = p; p = q; q = t; }
+                double4 ro = make_double4(1, 0, 1, 0);
+                if (q < k) {
+                    const double app = A[p * k + p].x, aqq = A[q * k + q].x;
+                    const double2 c = A[q * k + p];   // A[p][q]
+                    const double ac = sqrt(c.x * c.x + c.y * c.y);
+                    if (ac > 1e-300) {
+                        const double tau = (aqq - app) / (2.0 * ac);
+                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        const double cs = 1.0 / sqrt(1.0 + t * t);
+                        ro = make_double4(cs, t * cs, c.x / ac, c.y / ac);
+                    }
+                }
+                rot[i] = ro;
+                pr[i] = make_int2(p, q);
+            }
+            __syncthreads();
+            // columns: A <- A U, V <- V U with U on (p, q):
+            //   col p' = cs col p - sn e^{-i phi} col q ;  col q' = sn col p + cs e^{-i phi} col q
+            for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
+                const int i = e / k, row = e - i * k;
+                const int p = pr[i].x, q = pr[i].y;
+                if (q >= k) continue;
+                const double4 ro = rot[i];
+                const double2 em = make_double2(ro.z, -ro.w);   // e^{-i phi}
+                for (int w = 0; w < 2; ++w) {
+                    double2* M = w ? V : A;
+                    const double2 ap = M[p * k + row], aq = M[q * k + row];
+                    const double2 eq = cmul(em, aq);
+                    M[p * k + row] = make_double2(ro.x * ap.x - ro.y * eq.x, ro.x * ap.y - ro.y * eq.y);
+                    M[q * k + row] = make_double2(ro.y * ap.x + ro.x * eq.x, ro.y * ap.y + ro.x * eq.y);
+                }
+            }
+            __syncthreads();
+            // rows: A <- U^H A:  row p' = cs row p - sn e^{i phi} row q ; row q' = sn row p + cs e^{i phi} row q
+            for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
+                const int i = e / k, col = e - i * k;
+                const int p = pr[i].x, q = pr[i].y;
+                if (q >= k) continue;
+                const double4 ro = rot[i];
+                const double2 ep = make_double2(ro.z, ro.w);
+                const double2 ap = A[col * k + p], aq = A[col * k + q];
+                const double2 eq = cmul(ep, aq);
+                A[col * k + p] = make_double2(ro.x * ap.x - ro.y * eq.x, ro.x * ap.y - ro.y * eq.y);
+                A[col * k + q] = make_double2(ro.y * ap.x + ro.x * eq.x, ro.y * ap.y + ro.x * eq.y);
+            }
+            __syncthreads();
+        }
+    }
+    // sort by decreasing eigenvalue (selection order computed by thread 0)
+    __shared__ int order[64];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < k; ++i) order[i] = i;
+        for (int i = 0; i < k; ++i) {
+            int best = i;
+            for (int j = i + 1; j < k; ++j)
+                if (A[order[j] * k + order[j]].x > A[order[best] * k + order[best]].x) best = j;
+            const int t = order[i]; order[i] = order[best]; order[best] = t;
+        }
+    }
+    __syncthreads();
+    double* lam = lam_all + (long long)blockIdx.x * k;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int col = e / k, row = e - col * k;
+        G[e] = V[order[col] * k + row];
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) lam[i] = A[order[i] * k + order[i]].x;
+}
+
+// ---------------------------------------------------- Philox4x32-10 probes
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; k1 += W1; }
+        const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+        const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+template <typename C>
+__global__ void k_gaussian(C* __restrict__ dst, int m, int k, long long sD, int batch, uint32_t k0, uint32_t k1,
+                           const uint32_t* __restrict__ w2, const uint32_t* __restrict__ w3) {
+    typedef decltype(dst->x) R;
+    const long long per = (long long)m * k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * batch; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / per);
+        const long long r = e - b * per;
+        const int j = (int)(r / m), i = (int)(r - (long long)j * m);
+        uint32_t c[4] = {(uint32_t)(i >> 1), (uint32_t)j, w2[b], w3[b]};
+        philox10(c, k0, k1);
+        const uint32_t xa = (i & 1) ? c[2] : c[0], xb = (i & 1) ? c[3] : c[1];
+        C v;
+        if (sizeof(R) == 8) {
+            const double u1 = ((double)xa + 1.0) * 2.3283064365386963e-10;
+            const double u2 = (double)xb * 2.3283064365386963e-10;
+            const double rho = sqrt(-log(u1));
+            double s, cc;
+            sincospi(2.0 * u2, &s, &cc);
+            v.x = (R)(rho * cc);
+            v.y = (R)(rho * s);
+        } else {
+            const float u1 = ((float)xa + 1.0f) * 2.3283064365386963e-10f;
+            const float u2 = (float)xb * 2.3283064365386963e-10f;
+            const float rho = sqrtf(-logf(u1));
+            float s, cc;
+            sincospif(2.0f * u2, &s, &cc);
+            v.x = (R)(rho * cc);
+            v.y = (R)(rho * s);
+        }
+        dst[b * sD + r] = v;
+    }
+}
+
+// ------------------------------------------- blocked Gauss-Jordan inverse
+// Panel step: the panel's nb columns (all n rows) are held in shared memory
+// and reduced by Gauss-Jordan with partial pivoting over rows >= c.  The
+// result is the panel of the block step
+//     rows P:  A_PP^-1          rows R:  -A_RP A_PP^-1
+// (after the row swaps), with the swaps recorded in piv.
+template <typename C, int NT>
+__global__ void __launch_bounds__(NT)
+k_gj_panel(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* __restrict__ pivall) {
+    typedef decltype(Aall->x) R;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* pan = reinterpret_cast<C*>(sm_raw);        // n x nb, column-major (ld n)
+    __shared__ R rv[NT / 32];
+    __shared__ int ri[NT / 32];
+    __shared__ int pivrow;
+    __shared__ C rowc[64];
+    C* A = Aall + blockIdx.x * sA;
+    int* piv = pivall + (long long)blockIdx.x * n;
+    for (int e = threadIdx.x; e < n * nb; e += NT) {
+        const int j = e / n, i = e - j * n;
+        pan[e] = A[(long long)(k0 + j) * n + i];
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        const int c = k0 + j;
+        // argmax |pan[i][j]| over i >= c (first maximum wins)
+        R best = -1;
+        int bi = n;
+        for (int i = c + threadIdx.x; i < n; i += NT) {
+            const C v = pan[j * n + i];
+            const R a = v.x * v.x + v.y * v.y;
+            if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R b2 = rv[0];
+            int i2 = ri[0];
+            for (int w = 1; w < NT / 32; ++w)
+                if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
+            pivrow = i2 < n ? i2 : c;
+            piv[c] = pivrow;
+        }
+        __syncthreads();
+        const int p = pivrow;
+        if (p != c)
+            for (int t = threadIdx.x; t < nb; t += NT) {
+                const C a = pan[t * n + c];
+                pan[t * n + c] = pan[t * n + p];
+                pan[t * n + p] = a;
+            }
+        __syncthreads();
+        const C d = pan[j * n + c];
+        const R den = d.x * d.x + d.y * d.y;
+        const C inv = den > 0 ? mk(d.x / den, -d.y / den) : czero<C>();
+        for (int t = threadIdx.x; t < nb; t += NT) rowc[t] = t == j ? inv : cmul(pan[t * n + c], inv);
+        __syncthreads();
+        // columns other than j first (they read column j), then column j and row c
+        for (int e = threadIdx.x; e < n * nb; e += NT) {
+            const int t = e / n, i = e - t * n;
+            if (t == j || i == c) continue;
+            pan[e] = csub(pan[e], cmul(pan[j * n + i], rowc[t]));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += NT) {
+            if (i == c) continue;
+            const C f = pan[j * n + i];
+            pan[j * n + i] = mk(-(f.x * inv.x - f.y * inv.y), -(f.x * inv.y + f.y * inv.x));
+        }
+        for (int t = threadIdx.x; t < nb; t += NT) pan[t * n + c] = rowc[t];
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * nb; e += NT) {
+        const int j = e / n, i = e - j * n;
+        A[(long long)(k0 + j) * n + i] = pan[e];
+    }
+}
+
+// Apply the panel's swaps to every other column and copy its rows P aside.
+template <typename C>
+__global__ void k_gj_swap(C* __restrict__ Aall, int n, long long sA, int k0, int nb, const int* __restrict__ pivall,
+                          C* __restrict__ XPall) {
+    const int b = blockIdx.y;
+    C* A = Aall + b * sA;
+    const int* piv = pivall + (long long)b * n;
+    C* XP = XPall + (long long)b * nb * n;
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < n; col += gridDim.x * blockDim.x) {
+        if (col >= k0 && col < k0 + nb) continue;
+        C* a = A + (long long)col * n;
+        for (int j = 0; j < nb; ++j) {
+            const int c = k0 + j, p = piv[c];
+            if (p != c) { const C t = a[c]; a[c] = a[p]; a[p] = t; }
+        }
+        for (int j = 0; j < nb; ++j) XP[(long long)col * nb + j] = a[k0 + j];
+    }
+}
+
+// X_new = Pan * X_P + (rows outside P) X_old for every column outside P.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_gj_update(C* __restrict__ Aall, int n, long long sA, int k0, int nb, const C* __restrict__ XPall) {
+    __shared__ C Ps[64][17];
+    __shared__ C Xs[16][65];
+    const int b = blockIdx.z;
+    C* A = Aall + b * sA;
+    const C* XP = XPall + (long long)b * nb * n;
+    const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    C acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = czero<C>();
+    for (int t0 = 0; t0 < nb; t0 += 16) {
+        for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+            const int i = e % 64, t = e / 64;
+            const int gi = i0 + i;
+            Ps[i][t] = (gi < n && t0 + t < nb) ? A[(long long)(k0 + t0 + t) * n + gi] : czero<C>();
+            const int jj = e % 64, tt = e / 64;
+            const int gj = j0 + jj;
+            Xs[tt][jj] = (gj < n && t0 + tt < nb) ? XP[(long long)gj * nb + t0 + tt] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            C a[4], bb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = Ps[ty + 16 * q][t]; bb[q] = Xs[t][tx + 16 * q]; }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cfma(acc[p][q], a[p], bb[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+            if (gi >= n || gj >= n) continue;
+            if (gj >= k0 && gj < k0 + nb) continue;
+            C* a = A + (long long)gj * n + gi;
+            if (gi >= k0 && gi < k0 + nb) *a = acc[p][q];
+            else *a = cadd(*a, acc[p][q]);
+        }
+}
+
+// Undo the row interchanges as column interchanges in reverse order.
+template <typename C>
+__global__ void k_gj_unscramble(C* __restrict__ Aall, int n, long long sA, const int* __restrict__ pivall) {
+    const int b = blockIdx.y;
+    C* A = Aall + b * sA;
+    const int* piv = pivall + (long long)b * n;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        for (int c = n - 1; c >= 0; --c) {
+            const int p = piv[c];
+            if (p != c) {
+                const C t = A[(long long)c * n + row];
+                A[(long long)c * n + row] = A[(long long)p * n + row];
+                A[(long long)p * n + row] = t;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- norms
+template <typename C>
+__global__ void __launch_bounds__(256) k_norm_partial(const C* __restrict__ x, long long n, int nchunk, double* part) {
+    const int b = blockIdx.y, ch = blockIdx.x;
+    const long long per = (n + nchunk - 1) / nchunk;
+    const long long r0 = ch * per, r1 = min(n, r0 + per);
+    const C* xb = x + b * n;
+    double s = 0;
+    for (long long i = r0 + threadIdx.x; i < r1; i += 256) {
+        const C v = xb[i];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        part[(long long)b * nchunk + ch] = t;
+    }
+}
+
+__global__ void k_norm_reduce(const double* __restrict__ part, int nchunk, int batch, double* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    double s = 0;
+    for (int c = 0; c < nchunk; ++c) s += part[(long long)b * nchunk + c];
+    out[b] = s;
+}
+
+template <typename C>
+__global__ void k_cast64(const double2* __restrict__ s, C* __restrict__ d, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        C v;
+        v.x = s[e].x;
+        v.y = s[e].y;
+        d[e] = v;
+    }
+}
+
+}  // namespace
+
+// ================================================================ wrappers
+template <typename R>
+lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha,
+                const typename Cx<R>::T* A, int lda, long long sA,
+                const typename Cx<R>::T* B, int ldb, long long sB,
+                typename Cx<R>::T beta, typename Cx<R>::T* C, int ldc, long long sC,
+                int batch, cudaStream_t st) {
+    typedef typename Cx<R>::T CT;
+    if (m <= 0 || n <= 0 || batch <= 0) return LSW_OK;
+    const int oa = (opA == 'N' || opA == 'n') ? 0 : 1, ob = (opB == 'N' || opB == 'n') ? 0 : 1;
+    const int gx = (m + GBM - 1) / GBM, gy = (n + GBN - 1) / GBN;
+    if (k <= 0) {
+        // C = beta C
+        CT zero = czero<CT>();
+        k_gemm<CT><<<dim3(gx, gy, batch), 256, 0, st>>>(oa, ob, m, n, 0, zero, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                          sC, 1, 0, nullptr);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    // split K when the output grid alone cannot fill the GPU
+    int ksplit = 1;
+    const long long ctas = (long long)gx * gy * batch;
+    if (ctas < 304 && k >= 512) {
+        ksplit = (int)std::min<long long>((608 + ctas - 1) / ctas, (k + 255) / 256);
+        ksplit = std::max(1, std::min(ksplit, 64));
+    }
+    if (ksplit == 1) {
+        k_gemm<CT><<<dim3(gx, gy, batch), 256, 0, st>>>(oa, ob, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                          sC, 1, k, nullptr);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    int kchunk = (k + ksplit - 1) / ksplit;
+    kchunk = (kchunk + GBK - 1) / GBK * GBK;
+    ksplit = (k + kchunk - 1) / kchunk;
+    DevBuf part;
+    LSW_TRY(part.alloc(sizeof(CT) * (size_t)ksplit * batch * m * n, st));
+    k_gemm<CT><<<dim3(gx, gy, batch * ksplit), 256, 0, st>>>(oa, ob, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C,
+                                                               ldc, sC, ksplit, kchunk, part.as<CT>());
+    LSW_LAUNCH_CHECK();
+    k_gemm_reduce<CT><<<grid_for((long long)batch * m * n), 256, 0, st>>>(m, n, batch, ksplit, part.as<CT>(), alpha,
+                                                                          beta, C, ldc, sC);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int batch, typename Cx<R>::T*,
+                       cudaStream_t st) {
+    if (batch <= 0 || k <= 0 || m <= 0) return LSW_OK;
+    if (k > 64) return LSW_ERR_INVALID_ARG;
+    k_householder_qr<R, 512><<<batch, 512, 0, st>>>(A, m, k, sA);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st) {
+    typedef typename Cx<R>::T CT;
+    if (batch <= 0 || k <= 0) return LSW_OK;
+    if (k > 64) return LSW_ERR_INVALID_ARG;   // 16 entries per thread at 256 threads
+    const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
+    DevBuf part;
+    LSW_TRY(part.alloc(sizeof(double2) * (size_t)batch * nchunk * k * k, st));
+    k_gram_partial<CT><<<dim3(nchunk, batch), 256, sizeof(CT) * 32 * k, st>>>(Y, m, k, sY, nchunk,
+                                                                                part.as<double2>());
+    LSW_LAUNCH_CHECK();
+    k_gram_reduce<<<grid_for((long long)batch * k * k), 256, 0, st>>>(part.as<double2>(), nchunk, k * k, batch, G);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+lsw_status heev_jacobi(double2* G, double* lam, int k, int batch, cudaStream_t st) {
+    if (batch <= 0 || k <= 0) return LSW_OK;
+    if (k > 64) return LSW_ERR_INVALID_ARG;
+    const int m = (k + 1) & ~1;
+    const size_t sm = sizeof(double2) * 2 * k * k + sizeof(double4) * (m / 2) + sizeof(int2) * (m / 2);
+    static bool attr = false;
+    if (!attr) {
+        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr = true;
+    }
+    k_heev_jacobi<<<batch, 256, sm, st>>>(G, lam, k);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status cast_from64(const double2* src, typename Cx<R>::T* dst, long long n, cudaStream_t st) {
+    k_cast64<typename Cx<R>::T><<<grid_for(n), 256, 0, st>>>(src, dst, n);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status gaussian_fill(typename Cx<R>::T* dst, int m, int k, long long sD, int batch, uint64_t seed,
+                         const uint32_t* w2, const uint32_t* w3, cudaStream_t st) {
+    if (m <= 0 || k <= 0 || batch <= 0) return LSW_OK;
+    k_gaussian<typename Cx<R>::T><<<grid_for((long long)m * k * batch), 256, 0, st>>>(
+        dst, m, k, sD, batch, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), w2, w3);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cudaStream_t st) {
+    typedef typename Cx<R>::T CT;
+    if (n <= 0 || batch <= 0) return LSW_OK;
+    constexpr int NT = 1024;
+    const size_t cap = 200 * 1024;
+    int nb = 16;
+    while (nb > 1 && (size_t)n * nb * sizeof(CT) > cap) nb >>= 1;
+    if ((size_t)n * nb * sizeof(CT) > cap) return LSW_ERR_UNSUPPORTED_SIZE;
+    static bool attr = false;
+    if (!attr) {
+        LSW_CUDA(cudaFuncSetAttribute(k_gj_panel<CT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        attr = true;
+    }
+    DevBuf piv, xp;
+    LSW_TRY(piv.alloc(sizeof(int) * (size_t)n * batch, st));
+    LSW_TRY(xp.alloc(sizeof(CT) * (size_t)nb * n * batch, st));
+    for (int k0 = 0; k0 < n; k0 += nb) {
+        const int w = std::min(nb, n - k0);
+        k_gj_panel<CT, NT><<<batch, NT, sizeof(CT) * (size_t)n * w, st>>>(A, n, sA, k0, w, piv.as<int>());
+        LSW_LAUNCH_CHECK();
+        if (w == n) continue;
+        k_gj_swap<CT><<<dim3((n + 255) / 256, batch), 256, 0, st>>>(A, n, sA, k0, w, piv.as<int>(), xp.as<CT>());
+        LSW_LAUNCH_CHECK();
+        k_gj_update<CT><<<dim3((n + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(A, n, sA, k0, w, xp.as<CT>());
+        LSW_LAUNCH_CHECK();
+    }
+    k_gj_unscramble<CT><<<dim3((n + 255) / 256, batch), 256, 0, st>>>(A, n, sA, piv.as<int>());
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status norms2(const typename Cx<R>::T* x, long long n, int batch, double* out, cudaStream_t st) {
+    if (batch <= 0) return LSW_OK;
+    const int nchunk = (int)std::max<long long>(1, std::min<long long>((n + 4095) / 4096, std::max(1, 1216 / batch)));
+    DevBuf part;
+    LSW_TRY(part.alloc(sizeof(double) * (size_t)nchunk * batch, st));
+    k_norm_partial<typename Cx<R>::T><<<dim3(nchunk, batch), 256, 0, st>>>(x, n, nchunk, part.as<double>());
+    LSW_LAUNCH_CHECK();
+    k_norm_reduce<<<(batch + 255) / 256, 256, 0, st>>>(part.as<double>(), nchunk, batch, out);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+#define LSW_INST(R)                                                                                               \
+    template lsw_status gemm<R>(char, char, int, int, int, Cx<R>::T, const Cx<R>::T*, int, long long,             \
+                                const Cx<R>::T*, int, long long, Cx<R>::T, Cx<R>::T*, int, long long, int,        \
+                                cudaStream_t);                                                                    \
+    template lsw_status qr_explicit<R>(Cx<R>::T*, int, int, long long, int, Cx<R>::T*, cudaStream_t);             \
+    template lsw_status gram64<R>(const Cx<R>::T*, int, int, long long, int, double2*, cudaStream_t);             \
+    template lsw_status cast_from64<R>(const double2*, Cx<R>::T*, long long, cudaStream_t);                        \
+    template lsw_status gaussian_fill<R>(Cx<R>::T*, int, int, long long, int, uint64_t, const uint32_t*,          \
+                                         const uint32_t*, cudaStream_t);                                          \
+    template lsw_status inverse_gj<R>(Cx<R>::T*, int, long long, int, cudaStream_t);                              \
+    template lsw_status norms2<R>(const Cx<R>::T*, long long, int, double*, cudaStream_t);
+LSW_INST(float)
+LSW_INST(double)
+#undef LSW_INST
+
+}  // namespace lsw

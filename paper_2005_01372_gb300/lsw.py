@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "liblsw.so")
 C128, C64, MIXED = 0, 1, 2
 OP_FORWARD, OP_RESIDUAL, OP_PLAIN, OP_ADJOINT = 0, 1, 2, 3
 H_LOWRANK_SMW, H_HODLR = 0, 1
+SERIES, FGMRES = 0, 1
 SPLIT_QUADTREE, SPLIT_STRIPS = 0, 1
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "OOM", 4: "CUDA",
@@ -49,7 +50,8 @@ class _HParams(ctypes.Structure):
 
 class _SolveParams(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -149,9 +151,12 @@ class SolveParams:
     tol: float = 1e-6
     inner_tol: float = 1e-3
     max_outer: int = 8
+    method: int = 0
+    restart: int = 30
 
     def c(self):
-        return _SolveParams(self.prec, self.max_iter, self.tol, self.inner_tol, self.max_outer, 0)
+        return _SolveParams(self.prec, self.max_iter, self.tol, self.inner_tol, self.max_outer, self.method,
+                            self.restart, 0)
 
 
 class Green:
