@@ -115,6 +115,9 @@ typedef struct {
 const char* lsw_status_string(lsw_status s);
 /* Text of the last CUDA failure seen by the calling thread (diagnostics). */
 const char* lsw_last_error(void);
+/* Number of CUDA kernels the library has launched in this process
+ * (diagnostics; every call's kernels are counted as they are enqueued). */
+uint64_t lsw_launch_count(void);
 
 /* Green table and spectra (Sec. 2.2).
  * Tabulates the cell-integrated Green's function Gt at every offset

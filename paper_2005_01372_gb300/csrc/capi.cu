@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "lsw_internal.cuh"
@@ -11,6 +12,9 @@
 namespace lsw {
 
 static thread_local char g_last_error[512];
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
@@ -50,6 +54,8 @@ const char* lsw_status_string(lsw_status s) {
 // beyond diagnostics).
 const char* lsw_last_error(void) { return g_last_error; }
 
+uint64_t lsw_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out) {
     if (!grid || !out) return LSW_ERR_INVALID_ARG;
     *out = nullptr;
@@ -60,6 +66,16 @@ lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out) 
     lsw_green* g = new (std::nothrow) lsw_green();
     if (!g) return LSW_ERR_OOM;
     cudaGetDevice(&g->device);
+    {
+        // Scratch comes from the device's default stream-ordered pool; keep
+        // freed blocks cached there instead of unmapping them at every
+        // synchronisation, so repeated calls do not pay for new mappings.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     g->nz = grid->nz;
     g->nx = grid->nx;
     g->h = grid->h;

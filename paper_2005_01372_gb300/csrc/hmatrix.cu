@@ -544,8 +544,11 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
     // off-diagonal blocks of the inverse: -P T2^H and -T1 R^H
     const long long nn = (long long)m1 * r;
     k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(P.as<C>(), Hi.U[l + 1] + (size_t)a * nb1, nn, (R)-1);
+    LSW_LAUNCH_CHECK();
     k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(T2.as<C>(), Hi.W[l + 1] + (size_t)a * nb1, nn, (R)1);
+    LSW_LAUNCH_CHECK();
     k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(T1.as<C>(), Hi.U[l + 1] + (size_t)b * nb1, nn, (R)-1);
+    LSW_LAUNCH_CHECK();
     k_scale_copy<C><<<gridn(nn), 256, 0, st>>>(Rm.as<C>(), Hi.W[l + 1] + (size_t)b * nb1, nn, (R)1);
     LSW_LAUNCH_CHECK();
     return LSW_OK;

@@ -56,9 +56,16 @@ template <typename C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
         lsw_status s_ = (expr);                                    \
         if (s_ != LSW_OK) return s_;                               \
     } while (0)
-#define LSW_LAUNCH_CHECK() LSW_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by exactly one
+// LSW_LAUNCH_CHECK(), which also counts it (lsw_launch_count()).
+#define LSW_LAUNCH_CHECK()            \
+    do {                              \
+        lsw::count_launch();          \
+        LSW_CUDA(cudaGetLastError()); \
+    } while (0)
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+void count_launch();
 
 inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }

@@ -330,6 +330,7 @@ lsw_status fp64_residual(const lsw_green* g, const double* chi, const typename C
         LSW_TRY(u64.alloc(sizeof(double2) * n * nb, st));
         LSW_TRY(b64.alloc(sizeof(double2) * n * nb, st));
         k_scale_cast<C, double2><<<gridn(n * nb), 256, 0, st>>>(u, u64.as<double2>(), nullptr, n, nb);
+        LSW_LAUNCH_CHECK();
         k_scale_cast<C, double2><<<gridn(n * nb), 256, 0, st>>>(u0, b64.as<double2>(), nullptr, n, nb);
         LSW_LAUNCH_CHECK();
         pu = u64.as<double2>();

@@ -65,6 +65,7 @@ VP, I32, U32, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uin
 _SIGS = {
     "lsw_status_string": (ctypes.c_char_p, [I32]),
     "lsw_last_error": (ctypes.c_char_p, []),
+    "lsw_launch_count": (ctypes.c_uint64, []),
     "lsw_build_green": (I32, [ctypes.POINTER(_Grid), VP, ctypes.POINTER(VP)]),
     "lsw_destroy_green": (I32, [VP]),
     "lsw_green_table": (I32, [VP, VP, VP]),
@@ -201,6 +202,11 @@ class Green:
         _check(lib().lsw_point_sources(self._h, pos, len(positions), prec, _ptr(u0), _stream(stream)),
                "lsw_point_sources")
         return u0
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().lsw_launch_count())
 
 
 def build_green(nz, nx, h, c0, freq_hz, stream=None) -> Green:
