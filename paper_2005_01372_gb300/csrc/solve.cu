@@ -180,6 +180,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     LSW_TRY(hc.alloc(sizeof(C) * (m + 1) * nb, st));
     LSW_TRY(ysc.alloc(sizeof(double) * nb, st));
     LSW_TRY(yb.alloc(sizeof(C) * m * nb, st));
+    LSW_CUDA(cudaMemsetAsync(Zb.p, 0, sizeof(C) * n * m * nb, st));
     LSW_CUDA(cudaMemsetAsync(x, 0, sizeof(C) * n * nb, st));
     std::vector<double> nrmb, nr;
     LSW_TRY(host_norms<R>(b, n, nb, dn, nrmb, st));
@@ -302,9 +303,9 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
             }
         }
         LSW_CUDA(cudaMemcpyAsync(yb.p, yh.data(), sizeof(C) * m * nb, cudaMemcpyHostToDevice, st));
-        LSW_TRY(gemm<R>('N', 'N', (int)n, 1, m, one_, Zb.as<C>(), (int)n, n * m, yb.as<C>(), m, m, one_, x, (int)n, n, nb,
+        // only the j columns of Z written in this cycle take part
+        LSW_TRY(gemm<R>('N', 'N', (int)n, 1, j, one_, Zb.as<C>(), (int)n, n * m, yb.as<C>(), m, m, one_, x, (int)n, n, nb,
                         st));
-        (void)j;
     }
     return LSW_OK;
 }
