@@ -157,6 +157,25 @@ lsw_status lsw_apply_operator(const lsw_green* g, int prec, const double* chi,
                               const void* u, const void* u0, void* y,
                               int nbatch, int mode, void* stream);
 
+/* lsw_apply_operator without any device allocation.  The paper has no
+ * counterpart to this call.  It serves callers that cannot let a library
+ * allocate device memory while it runs: applications that reserve all device
+ * memory up front for their own allocator, embedders that audit the memory
+ * of every call, and latency-critical loops that cannot absorb an
+ * allocation's cost or its failure part-way through.  Arguments and results
+ * are those of lsw_apply_operator.  The scratch it needs (2 * nbatch * nz * nx
+ * complex values of prec) comes from one fixed 32 MiB device array that the
+ * library holds on every GPU that loads it, until the process exits; larger
+ * requests return LSW_ERR_UNSUPPORTED_SIZE without launching anything.
+ * The first call on a device looks up that array's device address (a runtime
+ * call that allocates nothing); make that first call before any stream
+ * capture.  Every call shares the one array, so calls whose work overlaps on
+ * the GPU (several streams or host threads) race on it: the caller must
+ * serialise them.  Nothing left by an earlier call needs clearing. */
+lsw_status lsw_apply_operator_noalloc(const lsw_green* g, int prec, const double* chi,
+                                      const void* u, const void* u0, void* y,
+                                      int nbatch, int mode, void* stream);
+
 /* Randomized range sketch of one block of G0 V (Algorithm 2): with s =
  * rows and t = cols (boxes inside the grid, unknowns numbered in strip order
  * inside each box), computes U (n_s x rank) and W (n_t x rank), column-major,

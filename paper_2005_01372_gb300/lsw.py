@@ -73,6 +73,7 @@ _SIGS = {
     "lsw_contrast": (I32, [VP, VP, VP, VP]),
     "lsw_point_sources": (I32, [VP, ctypes.POINTER(ctypes.c_int32), I32, I32, VP, VP]),
     "lsw_apply_operator": (I32, [VP, I32, VP, VP, VP, VP, I32, I32, VP]),
+    "lsw_apply_operator_noalloc": (I32, [VP, I32, VP, VP, VP, VP, I32, I32, VP]),
     "lsw_sketch_range": (I32, [VP, I32, VP, _Box, _Box, I32, I32, I32, U64, U32, VP, VP, VP]),
     "lsw_build_hmatrix": (I32, [VP, VP, ctypes.POINTER(_HParams), VP, ctypes.POINTER(VP)]),
     "lsw_destroy_hmatrix": (I32, [VP]),
@@ -222,6 +223,20 @@ def apply_operator(G: Green, chi, u, u0=None, mode: int = OP_PLAIN, y=None, stre
     _check(lib().lsw_apply_operator(G.handle, prec, _ptr(chi, torch.float64), _ptr(u, u.dtype),
                                     _ptr(u0, u.dtype) if u0 is not None else None, _ptr(y, u.dtype),
                                     nb, mode, _stream(stream)), "lsw_apply_operator")
+    return y
+
+
+def apply_operator_noalloc(G: Green, chi, u, u0=None, mode: int = OP_PLAIN, y=None, stream=None) -> torch.Tensor:
+    """lsw_apply_operator_noalloc: the same product as apply_operator with
+    the library's fixed device scratch, for callers that cannot let the
+    library allocate (the output y is still the caller's)."""
+    prec = C128 if u.dtype == torch.complex128 else C64
+    nb = u.numel() // G.n
+    if y is None:
+        y = torch.empty_like(u)
+    _check(lib().lsw_apply_operator_noalloc(G.handle, prec, _ptr(chi, torch.float64), _ptr(u, u.dtype),
+                                            _ptr(u0, u.dtype) if u0 is not None else None, _ptr(y, u.dtype),
+                                            nb, mode, _stream(stream)), "lsw_apply_operator_noalloc")
     return y
 
 
