@@ -112,6 +112,17 @@ template <typename R> struct HStore {
     }
 };
 
+// Low-rank updates that the inversion adds to the dense leaves of the matrix
+// being inverted (the Schur complements S = D - C A^-1 B), kept as factors:
+// leaf c accumulates U_c V_c^H with r columns per ancestor whose right
+// subtree holds it, stored left to right in the order they arrive.
+template <typename R> struct LeafUpd {
+    typedef typename Cx<R>::T C;
+    C* U = nullptr;   // nleaf x nL x kmax
+    C* V = nullptr;
+    int nL = 0, kmax = 0;
+};
+
 }  // namespace lsw
 
 struct lsw_hmatrix {
@@ -242,6 +253,29 @@ __global__ void k_concat(const C* __restrict__ U, const C* __restrict__ W, const
     }
 }
 
+// Leaves first..first+nleaf-1 receive X Y^H as factor columns [off, off + r).
+template <typename C>
+__global__ void k_leaf_append(const C* __restrict__ X, const C* __restrict__ Y, int m, int r, int nL, int nleaf,
+                              int first, int off, int kmax, C* __restrict__ U, C* __restrict__ V) {
+    const long long tot = (long long)nleaf * nL * r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int lf = (int)(e / ((long long)nL * r));
+        const long long q = e - (long long)lf * nL * r;
+        const int col = (int)(q / nL), i = (int)(q - (long long)col * nL);
+        const long long dst = ((long long)(first + lf) * kmax + off + col) * nL + i;
+        U[dst] = X[(long long)col * m + (long long)lf * nL + i];
+        V[dst] = Y[(long long)col * m + (long long)lf * nL + i];
+    }
+}
+
+template <typename C>
+__global__ void k_eye_plus(C* M, int r) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+        const int j = e / r, i = e - j * r;
+        if (i == j) M[e].x += 1;
+    }
+}
+
 template <typename C>
 __global__ void k_eye_minus(C* M, int r) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
@@ -283,20 +317,18 @@ lsw_status upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 
 // ------------------------------------------------------------- truncation
 // Best rank-r part of Q Yt^H for a batch of blocks (Q: nb x rp, Yt: mb x rp):
-// with Yt^H Yt = V diag(lam) V^H (FP64 Jacobi), keep the r leading
+// with Yt^H Yt = V diag(lam) V^H (FP64 Gram, Jacobi in precision R), keep the r leading
 // eigenvectors Vr:  U = alphaU Q Vr,  W = Yt Vr,  so U W^H = alphaU Q Vr Vr^H Yt^H.
 template <typename R>
 lsw_status truncate(const typename Cx<R>::T* Q, int nb, const typename Cx<R>::T* Yt, int mb, int rp, int r, int nblk,
                     typename Cx<R>::T alphaU, typename Cx<R>::T* Uout, long long sU, typename Cx<R>::T* Wout,
                     long long sW, cudaStream_t st) {
     typedef typename Cx<R>::T C;
-    DevBuf G, lam, V;
+    DevBuf G, V;
     LSW_TRY(G.alloc(sizeof(double2) * (size_t)nblk * rp * rp, st));
-    LSW_TRY(lam.alloc(sizeof(double) * (size_t)nblk * rp, st));
     LSW_TRY(V.alloc(sizeof(C) * (size_t)nblk * rp * rp, st));
     LSW_TRY(gram64<R>(Yt, mb, rp, (long long)mb * rp, nblk, G.as<double2>(), st));
-    LSW_TRY(heev_jacobi(G.as<double2>(), lam.as<double>(), rp, nblk, st));
-    LSW_TRY(cast_from64<R>(G.as<double2>(), V.as<C>(), (long long)nblk * rp * rp, st));
+    LSW_TRY(heev_jacobi<R>(G.as<double2>(), V.as<C>(), rp, nblk, st));
     const int rr = std::min(r, rp);
     if (rr < r) {
         LSW_CUDA(cudaMemsetAsync(Uout, 0, sizeof(C) * (size_t)sU * nblk, st));
@@ -451,14 +483,24 @@ lsw_status hmv_adj(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X,
 // back to rank r by Algorithm 1 (q = 0) through its factors.
 template <typename R>
 lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, const typename Cx<R>::T* Y, int op,
-                       int call_l, int call_c, int oversample, uint64_t seed, cudaStream_t st) {
+                       int call_l, int call_c, int oversample, uint64_t seed, cudaStream_t st,
+                       LeafUpd<R>* lu = nullptr) {
     typedef typename Cx<R>::T C;
     const int m = M.nl(l), L = M.L, r = M.r, nL = M.nl(L);
     const int rp = r + oversample;
     const int nleaf = 1 << (L - l);
-    C* D0 = M.D + (size_t)c * nleaf * nL * nL;
-    LSW_TRY(gemm<R>('N', 'C', nL, nL, r, one<C>(), X, m, nL, Y, m, nL, one<C>(), D0, nL, (long long)nL * nL, nleaf,
-                    st));
+    if (lu) {
+        // deferred: the leaves keep their inverses, the update goes to the
+        // factor lists, at the offset given by the right turns above call_l
+        const int off = r * __builtin_popcount((unsigned)call_c);
+        k_leaf_append<C><<<gridn((long long)nleaf * nL * r), 256, 0, st>>>(X, Y, m, r, nL, nleaf, c * nleaf, off,
+                                                                          lu->kmax, lu->U, lu->V);
+        LSW_LAUNCH_CHECK();
+    } else {
+        C* D0 = M.D + (size_t)c * nleaf * nL * nL;
+        LSW_TRY(gemm<R>('N', 'C', nL, nL, r, one<C>(), X, m, nL, Y, m, nL, one<C>(), D0, nL, (long long)nL * nL, nleaf,
+                        st));
+    }
     for (int lp = l + 1; lp <= L; ++lp) {
         const int cnt = 1 << (lp - l), nb = M.nl(lp);
         const size_t first = (size_t)c * cnt;
@@ -502,15 +544,40 @@ lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, c
 // block inversion).  X's node c+1 subtree is overwritten by the Schur
 // complement S = D - C A^-1 B.
 template <typename R>
-lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample, uint64_t seed, cudaStream_t st) {
+lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample, uint64_t seed, cudaStream_t st,
+                       LeafUpd<R>& lu) {
     typedef typename Cx<R>::T C;
     const int L = X.L, r = X.r;
     if (l == L) {
+        // X's leaf holds D^-1 (all original leaves are inverted together up
+        // front); the leaf to invert is S = D + U V^H with the k = r popcount(c)
+        // update columns its ancestors appended, so by Woodbury
+        //   S^-1 = D^-1 - D^-1 U (I + V^H D^-1 U)^-1 V^H D^-1.
         const int nL = X.nl(L);
-        C* d = Hi.D + (size_t)c * nL * nL;
-        k_copy<C><<<gridn((long long)nL * nL), 256, 0, st>>>(X.D + (size_t)c * nL * nL, d, (long long)nL * nL);
+        const long long nn = (long long)nL * nL;
+        const C* Di = X.D + (size_t)c * nn;
+        C* d = Hi.D + (size_t)c * nn;
+        LSW_CUDA(cudaMemcpyAsync(d, Di, sizeof(C) * nn, cudaMemcpyDeviceToDevice, st));
+        const int k = r * __builtin_popcount((unsigned)c);
+        if (k == 0) return LSW_OK;
+        const C* U = lu.U + (size_t)c * lu.kmax * nL;
+        const C* V = lu.V + (size_t)c * lu.kmax * nL;
+        DevBuf T1, T2, T3, M;
+        LSW_TRY(T1.alloc(sizeof(C) * (size_t)nL * k, st));
+        LSW_TRY(T2.alloc(sizeof(C) * (size_t)nL * k, st));
+        LSW_TRY(T3.alloc(sizeof(C) * (size_t)nL * k, st));
+        LSW_TRY(M.alloc(sizeof(C) * (size_t)k * k, st));
+        LSW_TRY(gemm<R>('N', 'N', nL, k, nL, one<C>(), Di, nL, 0, U, nL, 0, zero<C>(), T1.as<C>(), nL, 0, 1, st));
+        LSW_TRY(gemm<R>('C', 'N', k, k, nL, one<C>(), V, nL, 0, T1.as<C>(), nL, 0, zero<C>(), M.as<C>(), k, 0, 1, st));
+        k_eye_plus<C><<<gridn((long long)k * k), 256, 0, st>>>(M.as<C>(), k);
         LSW_LAUNCH_CHECK();
-        return inverse_gj<R>(d, nL, (long long)nL * nL, 1, st);
+        LSW_TRY(inverse_gj<R>(M.as<C>(), k, (long long)k * k, 1, st));
+        LSW_TRY(gemm<R>('C', 'N', k, nL, nL, one<C>(), V, nL, 0, Di, nL, 0, zero<C>(), T2.as<C>(), k, 0, 1, st));
+        LSW_TRY(gemm<R>('N', 'N', k, nL, k, one<C>(), M.as<C>(), k, 0, T2.as<C>(), k, 0, zero<C>(), T3.as<C>(), k, 0, 1,
+                        st));
+        LSW_TRY(gemm<R>('N', 'N', nL, nL, k, minus_one<C>(), T1.as<C>(), nL, 0, T3.as<C>(), k, 0, one<C>(), d, nL, 0, 1,
+                        st));
+        return LSW_OK;
     }
     const int a = 2 * c, b = 2 * c + 1, m1 = X.nl(l + 1);
     const int nb1 = m1 * r;
@@ -518,7 +585,7 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
     C* WB = X.W[l + 1] + (size_t)a * nb1;
     C* UC = X.U[l + 1] + (size_t)b * nb1;   // C = UC WC^H
     C* WC = X.W[l + 1] + (size_t)b * nb1;
-    LSW_TRY(invert_node<R>(X, l + 1, a, Hi, oversample, seed, st));
+    LSW_TRY(invert_node<R>(X, l + 1, a, Hi, oversample, seed, st, lu));
     DevBuf P, Rm, T1, T2, K, XK, T;
     const size_t vb = sizeof(C) * (size_t)m1 * r;
     LSW_TRY(P.alloc(vb, st));
@@ -533,8 +600,8 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
     LSW_TRY(gemm<R>('C', 'N', r, r, m1, one<C>(), WC, m1, 0, P.as<C>(), m1, 0, zero<C>(), K.as<C>(), r, 0, 1, st));
     // S = D - UC K WB^H  (in place on X's node b)
     LSW_TRY(gemm<R>('N', 'N', m1, r, r, minus_one<C>(), UC, m1, 0, K.as<C>(), r, 0, zero<C>(), XK.as<C>(), m1, 0, 1, st));
-    LSW_TRY(add_lowrank<R>(X, l + 1, b, XK.as<C>(), WB, 0, l, c, oversample, seed, st));
-    LSW_TRY(invert_node<R>(X, l + 1, b, Hi, oversample, seed, st));         // S^-1 into Hi
+    LSW_TRY(add_lowrank<R>(X, l + 1, b, XK.as<C>(), WB, 0, l, c, oversample, seed, st, &lu));
+    LSW_TRY(invert_node<R>(X, l + 1, b, Hi, oversample, seed, st, lu));     // S^-1 into Hi
     LSW_TRY(hmv<R>(Hi, l + 1, b, UC, r, T1.as<C>(), T.as<C>(), st));       // T1 = S^-1 UC
     LSW_TRY(hmv_adj<R>(Hi, l + 1, b, WB, r, T2.as<C>(), T.as<C>(), st));   // T2 = S^-H WB
     LSW_TRY(gemm<R>('C', 'N', r, r, m1, one<C>(), WB, m1, 0, T1.as<C>(), m1, 0, zero<C>(), K.as<C>(), r, 0, 1, st));
@@ -568,8 +635,22 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
     const int nL = tr.nl(L);
     k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, st>>>(g->table, g->nz, chi, h->perm_d, nL, 1 << L, X.D);
     LSW_LAUNCH_CHECK();
+    // every original leaf inverted at once; the inversion's Schur-complement
+    // leaves then follow by Woodbury from these
+    LSW_TRY(inverse_gj<R>(X.D, nL, (long long)nL * nL, 1 << L, st));
+    LeafUpd<R> lu;
+    lu.nL = nL;
+    lu.kmax = std::max(1, r * L);
+    DevBuf ub, vb;
+    const size_t lub = sizeof(C) * (size_t)(1 << L) * nL * lu.kmax;
+    LSW_TRY(ub.alloc(lub, st));
+    LSW_TRY(vb.alloc(lub, st));
+    LSW_CUDA(cudaMemsetAsync(ub.p, 0, lub, st));
+    LSW_CUDA(cudaMemsetAsync(vb.p, 0, lub, st));
+    lu.U = ub.as<C>();
+    lu.V = vb.as<C>();
     LSW_TRY(Hi.alloc(L, r, tr.n));
-    LSW_TRY(invert_node<R>(X, 0, 0, Hi, hp->oversample, hp->seed, st));
+    LSW_TRY(invert_node<R>(X, 0, 0, Hi, hp->oversample, hp->seed, st, lu));
     LSW_CUDA(cudaStreamSynchronize(st));
     return LSW_OK;
 }

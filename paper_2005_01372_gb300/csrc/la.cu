@@ -25,45 +25,45 @@ template <typename C> __device__ __forceinline__ C ldop(const C* p, bool conj_) 
 }
 
 // ------------------------------------------------------------------ GEMM
-// 64 x 64 output tile per CTA, 256 threads, 4 x 4 complex outputs per
+// BM x BN output tile per CTA, 256 threads, 4 x 4 complex outputs per
 // thread, K in steps of 8.  blockIdx.z = batch * ksplit + kpart; with
 // ksplit > 1 the partial products go to P (ksplit x batch x m x n) and a
 // second kernel reduces them in a fixed order.
-constexpr int GBM = 64, GBN = 64, GBK = 8;
+constexpr int GBK = 8;
 
-template <typename C>
+template <typename C, int BM, int BN>
 __global__ void __launch_bounds__(256)
 k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, int lda, long long sA,
        const C* __restrict__ B, int ldb, long long sB, C beta, C* __restrict__ Cm, int ldc, long long sC,
        int ksplit, int kchunk, C* __restrict__ P) {
-    __shared__ C As[GBK][GBM + 1];
-    __shared__ C Bs[GBK][GBN + 1];
+    static_assert((BM / 4) * (BN / 4) == 256, "256 threads of 4 x 4 outputs");
+    constexpr int TX = BN / 4, TY = BM / 4;
+    __shared__ C As[GBK][BM + 1];
+    __shared__ C Bs[GBK][BN + 1];
     const int bz = blockIdx.z;
     const int b = bz / ksplit, kp = bz - b * ksplit;
-    const int i0 = blockIdx.x * GBM, j0 = blockIdx.y * GBN;
+    const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
     const int kbeg = kp * kchunk, kend = min(k, kbeg + kchunk);
     const C* Ab = A + b * sA;
     const C* Bb = B + b * sB;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     C acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = czero<C>();
     for (int kk = kbeg; kk < kend; kk += GBK) {
-        // A tile: GBM x GBK  (element (i, kk+t))
-        for (int e = threadIdx.x; e < GBM * GBK; e += 256) {
+        for (int e = threadIdx.x; e < BM * GBK; e += 256) {
             int i, t;
-            if (opA == 0) { i = e % GBM; t = e / GBM; } else { t = e % GBK; i = e / GBK; }
+            if (opA == 0) { i = e % BM; t = e / BM; } else { t = e % GBK; i = e / GBK; }
             const int gi = i0 + i, gk = kk + t;
             C v = czero<C>();
             if (gi < m && gk < kend) v = opA == 0 ? Ab[(long long)gk * lda + gi] : ldop(Ab + (long long)gi * lda + gk, true);
             As[t][i] = v;
         }
-        // B tile: GBK x GBN  (element (kk+t, j))
-        for (int e = threadIdx.x; e < GBK * GBN; e += 256) {
+        for (int e = threadIdx.x; e < GBK * BN; e += 256) {
             int t, j;
-            if (opB == 0) { t = e % GBK; j = e / GBK; } else { j = e % GBN; t = e / GBN; }
+            if (opB == 0) { t = e % GBK; j = e / GBK; } else { j = e % BN; t = e / BN; }
             const int gj = j0 + j, gk = kk + t;
             C v = czero<C>();
             if (gj < n && gk < kend) v = opB == 0 ? Bb[(long long)gj * ldb + gk] : ldop(Bb + (long long)gk * ldb + gj, true);
@@ -74,7 +74,7 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
         for (int t = 0; t < GBK; ++t) {
             C a[4], bb[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { a[q] = As[t][ty + 16 * q]; bb[q] = Bs[t][tx + 16 * q]; }
+            for (int q = 0; q < 4; ++q) { a[q] = As[t][ty + TY * q]; bb[q] = Bs[t][tx + TX * q]; }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -86,7 +86,7 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
     for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+            const int gi = i0 + ty + TY * p, gj = j0 + tx + TX * q;
             if (gi < m && gj < n) {
                 if (ksplit == 1) {
                     C* c = Cm + b * sC + (long long)gj * ldc + gi;
@@ -98,6 +98,104 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
                 }
             }
         }
+}
+
+// C = A^H B partial sums for small outputs (m, n <= 64) and long K: CTA
+// (kpart, b) takes rows [k0, k1) of A (K x m) and B (K x n) in tiles of 32
+// rows through shared memory; thread t owns output entries t, t+256, ...
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_gemm_cn_small(int m, int n, int k, const C* __restrict__ A, int lda, long long sA, const C* __restrict__ B, int ldb,
+                long long sB, int kchunk, C* __restrict__ P, int batch) {
+    constexpr int TR = 32;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C (*As)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw);            // m rows
+    C (*Bs)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw) + m;        // n rows
+    const int kp = blockIdx.x, b = blockIdx.y;
+    const int k0 = kp * kchunk, k1 = min(k, k0 + kchunk);
+    const C* Ab = A + b * sA;
+    const C* Bb = B + b * sB;
+    const int nout = m * n;
+    C acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
+    for (int r0 = k0; r0 < k1; r0 += TR) {
+        const int nr = min(TR, k1 - r0);
+        for (int e = threadIdx.x; e < TR * m; e += 256) {
+            const int c = e / TR, r = e - c * TR;
+            As[c][r] = r < nr ? Ab[(long long)c * lda + r0 + r] : czero<C>();
+        }
+        for (int e = threadIdx.x; e < TR * n; e += 256) {
+            const int c = e / TR, r = e - c * TR;
+            Bs[c][r] = r < nr ? Bb[(long long)c * ldb + r0 + r] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int o = threadIdx.x + 256 * q;
+            if (o < nout) {
+                const int i = o % m, j = o / m;
+                C s = acc[q];
+                for (int r = 0; r < TR; ++r) cfmac(s, As[i][r], Bs[j][r]);
+                acc[q] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int o = threadIdx.x + 256 * q;
+        if (o < nout) {
+            const int i = o % m, j = o / m;
+            P[(((long long)kp * batch + b) * n + j) * m + i] = acc[q];
+        }
+    }
+}
+
+// C = alpha A B + beta C with a small inner dimension (k <= 64) and n <= 64:
+// B (k x n) sits in shared memory, thread (row, group of 16 columns) streams
+// its row of A.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_gemm_nn_smallk(int m, int n, int k, C alpha, const C* __restrict__ A, int lda, long long sA, const C* __restrict__ B,
+                 int ldb, long long sB, C beta, C* __restrict__ Cm, int ldc, long long sC) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* Bs = reinterpret_cast<C*>(sm_raw);       // k x n
+    const int b = blockIdx.y;
+    const C* Ab = A + b * sA;
+    const C* Bb = B + b * sB;
+    C* Cb = Cm + b * sC;
+    for (int e = threadIdx.x; e < k * n; e += 256) {
+        const int j = e / k, t = e - j * k;
+        Bs[j * k + t] = Bb[(long long)j * ldb + t];
+    }
+    __syncthreads();
+    const int ngrp = (n + 15) / 16;
+    const int rows_per = 256 / ngrp;           // rows handled by this CTA per pass
+    const int lr = threadIdx.x % rows_per, g = threadIdx.x / rows_per;
+    if (g >= ngrp) return;
+    const int i = blockIdx.x * rows_per + lr;
+    if (i >= m) return;
+    C acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
+    const int j0 = g * 16;
+    for (int t = 0; t < k; ++t) {
+        const C a = Ab[(long long)t * lda + i];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (j0 + q < n) cfma(acc[q], a, Bs[(j0 + q) * k + t]);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int j = j0 + q;
+        if (j < n) {
+            C* c = Cb + (long long)j * ldc + i;
+            C r = cmul(alpha, acc[q]);
+            if (beta.x != 0 || beta.y != 0) r = cadd(r, cmul(beta, *c));
+            *c = r;
+        }
+    }
 }
 
 template <typename C>
@@ -148,13 +246,16 @@ k_gram_partial(const C* __restrict__ Y, int m, int k, long long sY, int nchunk, 
                 const int i = pidx % k, j = pidx / k;
                 const C* yi = sy + i * TR;
                 const C* yj = sy + j * TR;
-                double sx = acc[q].x, syy = acc[q].y;
+                // products and the sum over one tile in the data's precision,
+                // tiles accumulated in FP64
+                typedef decltype(yi->x) R;
+                R sx = 0, syy = 0;
                 for (int r = 0; r < nr; ++r) {
-                    const double ax = yi[r].x, ay = yi[r].y, bx = yj[r].x, by = yj[r].y;
-                    sx += ax * bx + ay * by;
-                    syy += ax * by - ay * bx;
+                    const R ax = yi[r].x, ay = yi[r].y, bx = yj[r].x, by = yj[r].y;
+                    sx = fma(ax, bx, fma(ay, by, sx));
+                    syy = fma(ax, by, fma(-ay, bx, syy));
                 }
-                acc[q] = make_double2(sx, syy);
+                acc[q] = make_double2(acc[q].x + (double)sx, acc[q].y + (double)syy);
             }
         }
         __syncthreads();
@@ -208,14 +309,40 @@ __device__ __forceinline__ C block_sum(C v, C* red) {
     return s;
 }
 
+// Householder factorisation of A (m x k, ld m) in place, then the explicit
+// thin Q.  Rout (k x k, column-major), if given, receives R before Q
+// overwrites A.  Works on global or shared memory alike.
+// Sums of acc[0..nc) over the CTA (two barriers for all nc values); every
+// thread receives the sums in out[0..nc).
+template <typename C, int NT>
+__device__ __forceinline__ void block_sum16(const C* acc, int nc, C* red16 /* [NT/32][16] */, C* out) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        C v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        }
+        if (l == 0 && q < nc) red16[w * 16 + q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        C s = czero<C>();
+        for (int ww = 0; ww < NT / 32; ++ww) s = cadd(s, red16[ww * 16 + threadIdx.x]);
+        red16[(NT / 32) * 16 + threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int q = 0; q < nc; ++q) out[q] = red16[(NT / 32) * 16 + q];
+}
+
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT)
-k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA) {
+__device__ void hh_qr(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* Rout) {
     typedef typename Cx<R>::T C;
     __shared__ C red[33];
     __shared__ C tau_s[64];
-    __shared__ C wv[16];
-    C* A = Aall + blockIdx.x * sA;
+    __shared__ C red16[(NT / 32 + 1) * 16];
+    C wv[16];
     const int kk = min(k, m);
     // ---- factorisation
     for (int j = 0; j < kk; ++j) {
@@ -226,13 +353,12 @@ k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long s
         const C alpha = aj[j];
         C tau = czero<C>();
         R beta = alpha.x;
-        bool skip = (xnorm2 == 0 && alpha.y == 0);
+        const bool skip = (xnorm2 == 0 && alpha.y == 0);
         if (!skip) {
             const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
             beta = alpha.x >= 0 ? -nrm : nrm;
             tau = mk((beta - alpha.x) / beta, -alpha.y / beta);
-            // scale = 1 / (alpha - beta)
-            const C d = mk(alpha.x - beta, alpha.y);
+            const C d = mk(alpha.x - beta, alpha.y);       // scale x by 1 / (alpha - beta)
             const R den = d.x * d.x + d.y * d.y;
             const C sc = mk(d.x / den, -d.y / den);
             for (int i = j + 1 + threadIdx.x; i < m; i += NT) aj[i] = cmul(aj[i], sc);
@@ -256,11 +382,8 @@ k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long s
                 for (int q = 0; q < 16; ++q)
                     if (q < nc) cfmac(acc[q], v, A[(long long)(c0 + q) * m + i]);
             }
-            for (int q = 0; q < nc; ++q) {
-                C s = block_sum<C, NT>(acc[q], red);
-                if (threadIdx.x == 0) wv[q] = cmulc(tau, s);   // conj(tau) * (v^H a)
-            }
-            __syncthreads();
+            block_sum16<C, NT>(acc, nc, red16, wv);
+            for (int q = 0; q < nc; ++q) wv[q] = cmulc(tau, wv[q]);   // conj(tau) * (v^H a)
             for (int i = j + threadIdx.x; i < m; i += NT) {
                 const C v = i == j ? mk((R)1, (R)0) : aj[i];
                 for (int q = 0; q < nc; ++q) {
@@ -271,11 +394,17 @@ k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long s
             __syncthreads();
         }
     }
+    if (Rout) {
+        for (int e = threadIdx.x; e < k * k; e += NT) {
+            const int j = e / k, i = e - j * k;
+            Rout[e] = (i <= j && i < kk) ? A[(long long)j * m + i] : czero<C>();
+        }
+        __syncthreads();
+    }
     // ---- explicit Q = H_0 H_1 ... H_{k-1} [I; 0]
     for (int j = k - 1; j >= 0; --j) {
         C* aj = A + (long long)j * m;
-        if (j >= kk) {
-            // more columns than rows: column j of Q is zero
+        if (j >= kk) {          // more columns than rows: column j of Q is zero
             for (int i = threadIdx.x; i < m; i += NT) aj[i] = czero<C>();
             __syncthreads();
             continue;
@@ -292,11 +421,8 @@ k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long s
                 for (int q = 0; q < 16; ++q)
                     if (q < nc) cfmac(acc[q], v, A[(long long)(c0 + q) * m + i]);
             }
-            for (int q = 0; q < nc; ++q) {
-                C s = block_sum<C, NT>(acc[q], red);
-                if (threadIdx.x == 0) wv[q] = cmul(tau, s);      // tau * (v^H a)
-            }
-            __syncthreads();
+            block_sum16<C, NT>(acc, nc, red16, wv);
+            for (int q = 0; q < nc; ++q) wv[q] = cmul(tau, wv[q]);      // tau * (v^H a)
             for (int i = j + threadIdx.x; i < m; i += NT) {
                 const C v = i == j ? mk((R)1, (R)0) : aj[i];
                 for (int q = 0; q < nc; ++q) {
@@ -315,58 +441,139 @@ k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long s
     }
 }
 
-// --------------------------------------------- Jacobi eigen (Hermitian)
-// Parallel cyclic Jacobi: each round rotates k/2 disjoint index pairs chosen
-// by the circle method, so every pair is met once per sweep.
-__global__ void __launch_bounds__(256) k_heev_jacobi(double2* __restrict__ Gall, double* __restrict__ lam_all, int k) {
+// Chunk step of TSQR: rows [r0, r1) of block b (chunk ch of nch, sizes as
+// even as possible) are factored in shared memory; Q_chunk replaces them and
+// R_chunk goes to rows ch*k.. of the stacked matrix S_b ((nch*k) x k).
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT)
+k_tsqr_chunk(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA, int nch,
+             typename Cx<R>::T* __restrict__ Sall) {
+    typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int m = (k + 1) & ~1;                 // even number of players
-    double2* A = reinterpret_cast<double2*>(sm_raw);   // k x k, column-major
-    double2* V = A + k * k;
-    double4* rot = reinterpret_cast<double4*>(V + k * k);   // per pair: cs, sn, cos(phi), sin(phi)
-    int2* pr = reinterpret_cast<int2*>(rot + m / 2);
-    __shared__ double offn, totn;
-    double2* G = Gall + (long long)blockIdx.x * k * k;
-    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-        A[e] = G[e];
-        V[e] = make_double2((e % k) == (e / k) ? 1.0 : 0.0, 0.0);
+    const int b = blockIdx.y, ch = blockIdx.x;
+    const long long r0 = (long long)m * ch / nch, r1 = (long long)m * (ch + 1) / nch;
+    const int cc = (int)(r1 - r0);
+    C* Rs = reinterpret_cast<C*>(sm_raw);            // k x k
+    C* As = Rs + k * k;                               // cc x k
+    C* A = Aall + b * sA;
+    for (int e = threadIdx.x; e < cc * k; e += NT) {
+        const int j = e / cc, i = e - j * cc;
+        As[e] = A[(long long)j * m + r0 + i];
     }
     __syncthreads();
+    hh_qr<R, NT>(As, cc, k, Rs);
+    const int ms = nch * k;
+    C* S = Sall + (long long)b * ms * k;
+    for (int e = threadIdx.x; e < k * k; e += NT) {
+        const int j = e / k, i = e - j * k;
+        S[(long long)j * ms + ch * k + i] = Rs[e];
+    }
+    for (int e = threadIdx.x; e < cc * k; e += NT) {
+        const int j = e / cc, i = e - j * cc;
+        A[(long long)j * m + r0 + i] = As[e];
+    }
+}
+
+// Final TSQR step: Q_rows(chunk) = Q_chunk * Qtop[ch*k : ch*k + k, :].
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT)
+k_tsqr_apply(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA, int nch,
+             const typename Cx<R>::T* __restrict__ Sall) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int b = blockIdx.y, ch = blockIdx.x;
+    const long long r0 = (long long)m * ch / nch, r1 = (long long)m * (ch + 1) / nch;
+    const int cc = (int)(r1 - r0);
+    C* Ts = reinterpret_cast<C*>(sm_raw);            // k x k
+    C* As = Ts + k * k;                               // cc x k
+    C* A = Aall + b * sA;
+    const int ms = nch * k;
+    const C* S = Sall + (long long)b * ms * k;
+    for (int e = threadIdx.x; e < k * k; e += NT) {
+        const int j = e / k, i = e - j * k;
+        Ts[e] = S[(long long)j * ms + ch * k + i];
+    }
+    for (int e = threadIdx.x; e < cc * k; e += NT) {
+        const int j = e / cc, i = e - j * cc;
+        As[e] = A[(long long)j * m + r0 + i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cc * k; e += NT) {
+        const int j = e / cc, i = e - j * cc;
+        C acc = czero<C>();
+        for (int t = 0; t < k; ++t) cfma(acc, As[t * cc + i], Ts[j * k + t]);
+        A[(long long)j * m + r0 + i] = acc;
+    }
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT)
+k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA) {
+    hh_qr<R, NT>(Aall + blockIdx.x * sA, m, k, nullptr);
+}
+
+// --------------------------------------------- Jacobi eigen (Hermitian)
+// Parallel cyclic Jacobi in precision R: each round rotates k/2 disjoint
+// index pairs chosen by the circle method, so every pair is met once per
+// sweep.  Input: FP64 Hermitian G (k x k), scaled by its trace; output: the
+// eigenvectors as columns of V, by decreasing eigenvalue.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int m = (k + 1) & ~1;                 // even number of players
+    C* A = reinterpret_cast<C*>(sm_raw);        // k x k, column-major
+    C* V = A + k * k;
+    R* rot = reinterpret_cast<R*>(V + k * k);   // per pair: cs, sn, cos(phi), sin(phi)
+    int2* pr = reinterpret_cast<int2*>(rot + 4 * (m / 2));
+    __shared__ C red[33];
+    __shared__ double trs;
+    __shared__ int order[64];
+    const double2* G = Gall + (long long)blockIdx.x * k * k;
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < k; ++i) t += fabs(G[i * k + i].x);
+        trs = t > 0 ? 1.0 / t : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        A[e] = mk((R)(G[e].x * trs), (R)(G[e].y * trs));
+        V[e] = mk((R)((e % k) == (e / k) ? 1 : 0), (R)0);
+    }
+    __syncthreads();
+    const R tol = sizeof(R) == 8 ? (R)1e-30 : (R)1e-13;
     for (int sweep = 0; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0) {
-            double o = 0, t = 0;
-            for (int j = 0; j < k; ++j)
-                for (int i = 0; i < k; ++i) {
-                    const double2 a = A[j * k + i];
-                    const double v = a.x * a.x + a.y * a.y;
-                    t += v;
-                    if (i != j) o += v;
-                }
-            offn = o;
-            totn = t;
+        C part = czero<C>();
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            const C a = A[e];
+            const R v = a.x * a.x + a.y * a.y;
+            part.y += v;
+            if ((e % k) != (e / k)) part.x += v;
         }
-        __syncthreads();
-        if (!(offn > 1e-30 * totn) || totn == 0) break;
+        const C on = block_sum<C, 256>(part, red);
+        if (!(on.x > tol * on.y) || on.y == 0) break;
         for (int r = 0; r < m - 1; ++r) {
-            // pairs of this round
             for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
                 int p, q;
                 if (i == 0) { p = m - 1; q = r; }
                 else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
                 if (p > q) { const int t = p; p = q; q = t; }
-                double4 ro = make_double4(1, 0, 1, 0);
+                R cs = 1, sn = 0, cp = 1, spp = 0;
                 if (q < k) {
-                    const double app = A[p * k + p].x, aqq = A[q * k + q].x;
-                    const double2 c = A[q * k + p];   // A[p][q]
-                    const double ac = sqrt(c.x * c.x + c.y * c.y);
-                    if (ac > 1e-300) {
-                        const double tau = (aqq - app) / (2.0 * ac);
-                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        const double cs = 1.0 / sqrt(1.0 + t * t);
-                        ro = make_double4(cs, t * cs, c.x / ac, c.y / ac);
+                    const R app = A[p * k + p].x, aqq = A[q * k + q].x;
+                    const C c = A[q * k + p];   // A[p][q]
+                    const R ac = sqrt(c.x * c.x + c.y * c.y);
+                    if (ac > (R)1e-30 * (fabs(app) + fabs(aqq)) && ac > 0) {
+                        const R tau = (aqq - app) / (2 * ac);
+                        const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+                        cs = (R)1 / sqrt((R)1 + t * t);
+                        sn = t * cs;
+                        cp = c.x / ac;
+                        spp = c.y / ac;
                     }
                 }
-                rot[i] = ro;
+                rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
                 pr[i] = make_int2(p, q);
             }
             __syncthreads();
@@ -376,14 +583,14 @@ __global__ void __launch_bounds__(256) k_heev_jacobi(double2* __restrict__ Gall,
                 const int i = e / k, row = e - i * k;
                 const int p = pr[i].x, q = pr[i].y;
                 if (q >= k) continue;
-                const double4 ro = rot[i];
-                const double2 em = make_double2(ro.z, -ro.w);   // e^{-i phi}
+                const R cs = rot[4 * i], sn = rot[4 * i + 1];
+                const C em = mk(rot[4 * i + 2], -rot[4 * i + 3]);   // e^{-i phi}
                 for (int w = 0; w < 2; ++w) {
-                    double2* M = w ? V : A;
-                    const double2 ap = M[p * k + row], aq = M[q * k + row];
-                    const double2 eq = cmul(em, aq);
-                    M[p * k + row] = make_double2(ro.x * ap.x - ro.y * eq.x, ro.x * ap.y - ro.y * eq.y);
-                    M[q * k + row] = make_double2(ro.y * ap.x + ro.x * eq.x, ro.y * ap.y + ro.x * eq.y);
+                    C* M = w ? V : A;
+                    const C ap = M[p * k + row], aq = M[q * k + row];
+                    const C eq = cmul(em, aq);
+                    M[p * k + row] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
+                    M[q * k + row] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
                 }
             }
             __syncthreads();
@@ -392,18 +599,16 @@ __global__ void __launch_bounds__(256) k_heev_jacobi(double2* __restrict__ Gall,
                 const int i = e / k, col = e - i * k;
                 const int p = pr[i].x, q = pr[i].y;
                 if (q >= k) continue;
-                const double4 ro = rot[i];
-                const double2 ep = make_double2(ro.z, ro.w);
-                const double2 ap = A[col * k + p], aq = A[col * k + q];
-                const double2 eq = cmul(ep, aq);
-                A[col * k + p] = make_double2(ro.x * ap.x - ro.y * eq.x, ro.x * ap.y - ro.y * eq.y);
-                A[col * k + q] = make_double2(ro.y * ap.x + ro.x * eq.x, ro.y * ap.y + ro.x * eq.y);
+                const R cs = rot[4 * i], sn = rot[4 * i + 1];
+                const C ep = mk(rot[4 * i + 2], rot[4 * i + 3]);
+                const C ap = A[col * k + p], aq = A[col * k + q];
+                const C eq = cmul(ep, aq);
+                A[col * k + p] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
+                A[col * k + q] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
             }
             __syncthreads();
         }
     }
-    // sort by decreasing eigenvalue (selection order computed by thread 0)
-    __shared__ int order[64];
     if (threadIdx.x == 0) {
         for (int i = 0; i < k; ++i) order[i] = i;
         for (int i = 0; i < k; ++i) {
@@ -414,12 +619,11 @@ __global__ void __launch_bounds__(256) k_heev_jacobi(double2* __restrict__ Gall,
         }
     }
     __syncthreads();
-    double* lam = lam_all + (long long)blockIdx.x * k;
+    C* Vo = Vall + (long long)blockIdx.x * k * k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         const int col = e / k, row = e - col * k;
-        G[e] = V[order[col] * k + row];
+        Vo[e] = V[order[col] * k + row];
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) lam[i] = A[order[i] * k + order[i]].x;
 }
 
 // ---------------------------------------------------- Philox4x32-10 probes
@@ -550,6 +754,186 @@ k_gj_panel(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* __res
         const int j = e / n, i = e - j * n;
         A[(long long)(k0 + j) * n + i] = pan[e];
     }
+}
+
+// Register-resident panel step for n <= NT: thread i holds row i of the
+// nb (<= 16) panel columns.  Each pivot step is an argmax over the rows at
+// or below the pivot, a row exchange between two threads, and an update of
+// every row by the scaled pivot row -- four barriers per column.
+template <typename C, int NT, int NB>
+__global__ void __launch_bounds__(NT)
+k_gj_panel_reg(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* __restrict__ pivall) {
+    typedef decltype(Aall->x) R;
+    __shared__ R wbest[NT / 32];
+    __shared__ int widx[NT / 32];
+    __shared__ int pivrow;
+    __shared__ C rowc[NB];
+    __shared__ C xbuf[2][NB];
+    C* A = Aall + blockIdx.x * sA;
+    int* piv = pivall + (long long)blockIdx.x * n;
+    const int i = threadIdx.x;
+    const bool own = i < n;
+    C prow[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) prow[t] = (own && t < nb) ? A[(long long)(k0 + t) * n + i] : czero<C>();
+    for (int j = 0; j < nb; ++j) {
+        const int c = k0 + j;
+        C pj = czero<C>();
+#pragma unroll
+        for (int t = 0; t < NB; ++t) if (t == j) pj = prow[t];
+        R best = (own && i >= c) ? pj.x * pj.x + pj.y * pj.y : (R)-1;
+        int bi = (own && i >= c) ? i : n;
+        for (int o = 16; o > 0; o >>= 1) {
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((i & 31) == 0) { wbest[i >> 5] = best; widx[i >> 5] = bi; }
+        __syncthreads();
+        if (i < 32) {
+            R b2 = i < NT / 32 ? wbest[i] : (R)-1;
+            int i2 = i < NT / 32 ? widx[i] : n;
+            for (int o = 16; o > 0; o >>= 1) {
+                const R ob = __shfl_xor_sync(0xffffffffu, b2, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, i2, o);
+                if (ob > b2 || (ob == b2 && oi < i2)) { b2 = ob; i2 = oi; }
+            }
+            if (i == 0) {
+                pivrow = i2 < n ? i2 : c;
+                piv[c] = pivrow;
+            }
+        }
+        __syncthreads();
+        const int p = pivrow;
+        if (p != c) {
+            if (i == c) {
+#pragma unroll
+                for (int t = 0; t < NB; ++t) xbuf[0][t] = prow[t];
+            }
+            if (i == p) {
+#pragma unroll
+                for (int t = 0; t < NB; ++t) xbuf[1][t] = prow[t];
+            }
+            __syncthreads();
+            if (i == c) {
+#pragma unroll
+                for (int t = 0; t < NB; ++t) prow[t] = xbuf[1][t];
+            }
+            if (i == p) {
+#pragma unroll
+                for (int t = 0; t < NB; ++t) prow[t] = xbuf[0][t];
+            }
+        }
+        if (i == c) {
+            C d = czero<C>();
+#pragma unroll
+            for (int t = 0; t < NB; ++t) if (t == j) d = prow[t];
+            const R den = d.x * d.x + d.y * d.y;
+            const C inv = den > 0 ? mk(d.x / den, -d.y / den) : czero<C>();
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                prow[t] = t == j ? inv : cmul(prow[t], inv);
+                rowc[t] = prow[t];
+            }
+        }
+        __syncthreads();
+        if (own && i != c) {
+            const C inv = rowc[j];
+            C f = czero<C>();
+#pragma unroll
+            for (int t = 0; t < NB; ++t) if (t == j) f = prow[t];
+#pragma unroll
+            for (int t = 0; t < NB; ++t) {
+                if (t == j) prow[t] = mk(-(f.x * inv.x - f.y * inv.y), -(f.x * inv.y + f.y * inv.x));
+                else if (t < nb) prow[t] = csub(prow[t], cmul(f, rowc[t]));
+            }
+        }
+    }
+    if (own) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+            if (t < nb) A[(long long)(k0 + t) * n + i] = prow[t];
+    }
+}
+
+// Out-of-place block step for every column outside the panel, with the
+// panel's row swaps folded into the reads:  row i of the result is
+//   (i outside P) X[sigma(i)] + sum_t Pan[i][t] X[sigma(k0 + t)],
+// sigma the composition of the swaps; panel columns are copied.
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_gj_update_oop(const C* __restrict__ Ain, C* __restrict__ Aout, int n, long long sA, int k0, int nb,
+                const int* __restrict__ pivall) {
+    __shared__ C Ps[64][17];
+    __shared__ C Xs[16][65];
+    __shared__ int rmap[64];
+    __shared__ int pmap[16];
+    __shared__ int sw_pos[32], sw_val[32];
+    __shared__ int nsw;
+    const int b = blockIdx.z;
+    const C* A = Ain + b * sA;
+    C* O = Aout + b * sA;
+    const int* piv = pivall + (long long)b * n;
+    const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+    if (threadIdx.x == 0) {
+        // sigma on the positions the swaps touch
+        int cnt = 0;
+        for (int j = 0; j < nb; ++j) {
+            const int c = k0 + j, p = piv[c];
+            if (p == c) continue;
+            int ic = -1, ip = -1;
+            for (int q = 0; q < cnt; ++q) { if (sw_pos[q] == c) ic = q; if (sw_pos[q] == p) ip = q; }
+            if (ic < 0) { sw_pos[cnt] = c; sw_val[cnt] = c; ic = cnt++; }
+            if (ip < 0) { sw_pos[cnt] = p; sw_val[cnt] = p; ip = cnt++; }
+            const int t = sw_val[ic]; sw_val[ic] = sw_val[ip]; sw_val[ip] = t;
+        }
+        nsw = cnt;
+    }
+    __syncthreads();
+    auto sigma = [&](int pos) {
+        for (int q = 0; q < nsw; ++q) if (sw_pos[q] == pos) return sw_val[q];
+        return pos;
+    };
+    if (threadIdx.x < 64) rmap[threadIdx.x] = i0 + threadIdx.x < n ? sigma(i0 + threadIdx.x) : 0;
+    if (threadIdx.x < 16) pmap[threadIdx.x] = threadIdx.x < nb ? sigma(k0 + threadIdx.x) : 0;
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    C acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = czero<C>();
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+        const int ii = e % 64, t = e / 64;
+        const int gi = i0 + ii;
+        Ps[ii][t] = (gi < n && t < nb) ? A[(long long)(k0 + t) * n + gi] : czero<C>();
+        const int jj = e % 64;
+        const int gj = j0 + jj;
+        Xs[t][jj] = (gj < n && t < nb) ? A[(long long)gj * n + pmap[t]] : czero<C>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        C a[4], bb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { a[q] = Ps[ty + 16 * q][t]; bb[q] = Xs[t][tx + 16 * q]; }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cfma(acc[p][q], a[p], bb[q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int li = ty + 16 * p;
+            const int gi = i0 + li, gj = j0 + tx + 16 * q;
+            if (gi >= n || gj >= n) continue;
+            C* o = O + (long long)gj * n + gi;
+            if (gj >= k0 && gj < k0 + nb) { *o = A[(long long)gj * n + gi]; continue; }
+            if (gi >= k0 && gi < k0 + nb) *o = acc[p][q];
+            else *o = cadd(A[(long long)gj * n + rmap[li]], acc[p][q]);
+        }
 }
 
 // Apply the panel's swaps to every other column and copy its rows P aside.
@@ -693,15 +1077,59 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
     typedef typename Cx<R>::T CT;
     if (m <= 0 || n <= 0 || batch <= 0) return LSW_OK;
     const int oa = (opA == 'N' || opA == 'n') ? 0 : 1, ob = (opB == 'N' || opB == 'n') ? 0 : 1;
-    const int gx = (m + GBM - 1) / GBM, gy = (n + GBN - 1) / GBN;
     if (k <= 0) {
         // C = beta C
-        CT zero = czero<CT>();
-        k_gemm<CT><<<dim3(gx, gy, batch), 256, 0, st>>>(oa, ob, m, n, 0, zero, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                          sC, 1, 0, nullptr);
+        const CT zero = czero<CT>();
+        k_gemm<CT, 64, 64><<<dim3((m + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(
+            oa, ob, m, n, 0, zero, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 1, 0, nullptr);
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
+    // long inner products with a small result: split K, reduce in order
+    if (oa == 1 && ob == 0 && m <= 64 && n <= 64 && (long long)m * n <= 4096 && k >= 128) {
+        const long long want = std::max<long long>(1, 1216 / batch);
+        const int kchunk = (int)std::max<long long>(256, ((k + want - 1) / want + 31) / 32 * 32);
+        const int ksplit = (k + kchunk - 1) / kchunk;
+        DevBuf part;
+        LSW_TRY(part.alloc(sizeof(CT) * (size_t)ksplit * batch * m * n, st));
+        static bool attr_cn[2] = {false, false};
+        if (!attr_cn[sizeof(R) == 8]) {
+            LSW_CUDA(cudaFuncSetAttribute(k_gemm_cn_small<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            attr_cn[sizeof(R) == 8] = true;
+        }
+        k_gemm_cn_small<CT><<<dim3(ksplit, batch), 256, sizeof(CT) * 33 * (m + n), st>>>(m, n, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(),
+                                                                   batch);
+        LSW_LAUNCH_CHECK();
+        k_gemm_reduce<CT><<<grid_for((long long)batch * m * n), 256, 0, st>>>(m, n, batch, ksplit, part.as<CT>(), alpha,
+                                                                              beta, C, ldc, sC);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    // tall times small
+    if (oa == 0 && ob == 0 && k <= 64 && n <= 64) {
+        const int ngrp = (n + 15) / 16;
+        const int rows_per = 256 / ngrp;
+        static bool attr_nn[2] = {false, false};
+        if (!attr_nn[sizeof(R) == 8]) {
+            LSW_CUDA(cudaFuncSetAttribute(k_gemm_nn_smallk<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            attr_nn[sizeof(R) == 8] = true;
+        }
+        k_gemm_nn_smallk<CT><<<dim3((m + rows_per - 1) / rows_per, batch), 256, sizeof(CT) * k * n, st>>>(
+            m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    const bool narrow = n <= 32;
+    const int BMv = narrow ? 128 : 64, BNv = narrow ? 32 : 64;
+    const int gx = (m + BMv - 1) / BMv, gy = (n + BNv - 1) / BNv;
+    auto launch = [&](int ks, int kc, CT* P) {
+        if (narrow)
+            k_gemm<CT, 128, 32><<<dim3(gx, gy, batch * ks), 256, 0, st>>>(oa, ob, m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                                           beta, C, ldc, sC, ks, kc, P);
+        else
+            k_gemm<CT, 64, 64><<<dim3(gx, gy, batch * ks), 256, 0, st>>>(oa, ob, m, n, k, alpha, A, lda, sA, B, ldb, sB,
+                                                                          beta, C, ldc, sC, ks, kc, P);
+    };
     // split K when the output grid alone cannot fill the GPU
     int ksplit = 1;
     const long long ctas = (long long)gx * gy * batch;
@@ -710,8 +1138,7 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
         ksplit = std::max(1, std::min(ksplit, 64));
     }
     if (ksplit == 1) {
-        k_gemm<CT><<<dim3(gx, gy, batch), 256, 0, st>>>(oa, ob, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                          sC, 1, k, nullptr);
+        launch(1, k, nullptr);
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
@@ -720,8 +1147,7 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
     ksplit = (k + kchunk - 1) / kchunk;
     DevBuf part;
     LSW_TRY(part.alloc(sizeof(CT) * (size_t)ksplit * batch * m * n, st));
-    k_gemm<CT><<<dim3(gx, gy, batch * ksplit), 256, 0, st>>>(oa, ob, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C,
-                                                               ldc, sC, ksplit, kchunk, part.as<CT>());
+    launch(ksplit, kchunk, part.as<CT>());
     LSW_LAUNCH_CHECK();
     k_gemm_reduce<CT><<<grid_for((long long)batch * m * n), 256, 0, st>>>(m, n, batch, ksplit, part.as<CT>(), alpha,
                                                                           beta, C, ldc, sC);
@@ -730,11 +1156,40 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
 }
 
 template <typename R>
-lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int batch, typename Cx<R>::T*,
+lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int batch, typename Cx<R>::T* work,
                        cudaStream_t st) {
+    typedef typename Cx<R>::T CT;
     if (batch <= 0 || k <= 0 || m <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
-    k_householder_qr<R, 512><<<batch, 512, 0, st>>>(A, m, k, sA);
+    (void)work;
+    constexpr int NT = 256;
+    const size_t cap = 200 * 1024;
+    int cmax = (int)std::min<size_t>(1024, (cap / sizeof(CT) - (size_t)k * k) / k);
+    static bool attr[2] = {false, false};
+    if (!attr[sizeof(R) == 8]) {
+        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_chunk<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_apply<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        attr[sizeof(R) == 8] = true;
+    }
+    // Tall-skinny QR (TSQR): factor row chunks independently, then the
+    // stacked R factors, then combine.  Every chunk has >= cmax/2 >= k rows.
+    const int nch = (m + cmax - 1) / cmax;
+    const int rows = (m + nch - 1) / nch;
+    const size_t smem = sizeof(CT) * ((size_t)rows * k + (size_t)k * k);
+    if (nch == 1) {
+        DevBuf S;
+        LSW_TRY(S.alloc(sizeof(CT) * (size_t)batch * k * k, st));
+        k_tsqr_chunk<R, NT><<<dim3(1, batch), NT, smem, st>>>(A, m, k, sA, 1, S.as<CT>());
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    DevBuf S;
+    const int ms = nch * k;
+    LSW_TRY(S.alloc(sizeof(CT) * (size_t)batch * ms * k, st));
+    k_tsqr_chunk<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
+    LSW_LAUNCH_CHECK();
+    LSW_TRY(qr_explicit<R>(S.as<CT>(), ms, k, (long long)ms * k, batch, nullptr, st));
+    k_tsqr_apply<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
@@ -755,17 +1210,19 @@ lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int ba
     return LSW_OK;
 }
 
-lsw_status heev_jacobi(double2* G, double* lam, int k, int batch, cudaStream_t st) {
+template <typename R>
+lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st) {
+    typedef typename Cx<R>::T CT;
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
     const int m = (k + 1) & ~1;
-    const size_t sm = sizeof(double2) * 2 * k * k + sizeof(double4) * (m / 2) + sizeof(int2) * (m / 2);
-    static bool attr = false;
-    if (!attr) {
-        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        attr = true;
+    const size_t sm = sizeof(CT) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2);
+    static bool attr[2] = {false, false};
+    if (!attr[sizeof(R) == 8]) {
+        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr[sizeof(R) == 8] = true;
     }
-    k_heev_jacobi<<<batch, 256, sm, st>>>(G, lam, k);
+    k_heev_jacobi<R><<<batch, 256, sm, st>>>(G, V, k);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
@@ -792,6 +1249,33 @@ lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cuda
     typedef typename Cx<R>::T CT;
     if (n <= 0 || batch <= 0) return LSW_OK;
     constexpr int NT = 1024;
+    if (n <= NT) {
+        // register panels + out-of-place updates, ping-pong between A and B
+        constexpr int NB = sizeof(R) == 8 ? 8 : 16;
+        const int nb = NB;
+        DevBuf piv, B;
+        LSW_TRY(piv.alloc(sizeof(int) * (size_t)n * batch, st));
+        LSW_TRY(B.alloc(sizeof(CT) * (size_t)sA * batch, st));
+        CT* cur = A;
+        CT* nxt = B.as<CT>();
+        for (int k0 = 0; k0 < n; k0 += nb) {
+            const int w = std::min(nb, n - k0);
+            k_gj_panel_reg<CT, NT, NB><<<batch, NT, 0, st>>>(cur, n, sA, k0, w, piv.as<int>());
+            LSW_LAUNCH_CHECK();
+            if (w == n) continue;
+            k_gj_update_oop<CT><<<dim3((n + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(cur, nxt, n, sA, k0, w,
+                                                                                          piv.as<int>());
+            LSW_LAUNCH_CHECK();
+            std::swap(cur, nxt);
+        }
+        if (cur != A) {
+            LSW_CUDA(cudaMemcpy2DAsync(A, sizeof(CT) * sA, cur, sizeof(CT) * sA, sizeof(CT) * (size_t)n * n, batch,
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+        k_gj_unscramble<CT><<<dim3((n + 255) / 256, batch), 256, 0, st>>>(A, n, sA, piv.as<int>());
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
     const size_t cap = 200 * 1024;
     int nb = 16;
     while (nb > 1 && (size_t)n * nb * sizeof(CT) > cap) nb >>= 1;
@@ -838,6 +1322,7 @@ lsw_status norms2(const typename Cx<R>::T* x, long long n, int batch, double* ou
                                 cudaStream_t);                                                                    \
     template lsw_status qr_explicit<R>(Cx<R>::T*, int, int, long long, int, Cx<R>::T*, cudaStream_t);             \
     template lsw_status gram64<R>(const Cx<R>::T*, int, int, long long, int, double2*, cudaStream_t);             \
+    template lsw_status heev_jacobi<R>(const double2*, Cx<R>::T*, int, int, cudaStream_t);                        \
     template lsw_status cast_from64<R>(const double2*, Cx<R>::T*, long long, cudaStream_t);                        \
     template lsw_status gaussian_fill<R>(Cx<R>::T*, int, int, long long, int, uint64_t, const uint32_t*,          \
                                          const uint32_t*, cudaStream_t);                                          \

@@ -156,10 +156,11 @@ template <typename R>
 lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int batch,
                   double2* G, cudaStream_t st);
 
-// Batched Hermitian eigen-decomposition by cyclic Jacobi in FP64: G_b (k x k)
-// is replaced by its eigenvectors (columns), sorted by decreasing eigenvalue;
-// lam_b receives the eigenvalues.
-lsw_status heev_jacobi(double2* G, double* lam, int k, int batch, cudaStream_t st);
+// Batched Hermitian eigenvectors by cyclic Jacobi in precision R: V_b (k x k)
+// receives the eigenvectors of the FP64 matrix G_b as columns, sorted by
+// decreasing eigenvalue.
+template <typename R>
+lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st);
 
 // Cast FP64 complex -> working precision.
 template <typename R>
