@@ -112,4 +112,73 @@ __device__ void smem_fft(C* s, int lstride, int nlines, int P, int logP,
     }
 }
 
+// ------------------------------------------------------------------------
+// Register-resident line FFT.  A line of length P = 2^logP (8 <= P <= 2048)
+// is held by T = P / 8 threads, thread t owning v[r] = x[t + r T].  One
+// radix-2 or radix-4 stage (when log2 P is not a multiple of 3) is followed
+// by radix-8 stages; between stages the line passes once through shared
+// memory, indexed with one pad slot per 8 entries so that the strided
+// Stockham stores spread over the banks.  The result comes back in the same
+// layout, v[r] = X[t + r T]; the last stage needs no exchange.
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+
+template <typename C>
+__device__ __forceinline__ void exch(C v[8], C* s, int t, int T) {
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = s[pad8(t + r * T)];
+    __syncthreads();
+}
+
+template <typename C, int LOGP>
+__device__ __forceinline__ void fft_line(C v[8], C* s, int t, const C* __restrict__ tw, int twstep, bool inv) {
+    constexpr int P = 1 << LOGP;
+    constexpr int T = P >> 3;
+    constexpr int B = 1 << (LOGP % 3);
+    int Ns = 1;
+    if (B == 2) {
+        // four radix-2 butterflies j = t + qT: inputs v[q], v[q + 4]; outputs y[2j], y[2j + 1]
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const C a = v[q], c = v[q + 4];
+            const int j = t + q * T;
+            s[pad8(2 * j)] = cadd(a, c);
+            s[pad8(2 * j + 1)] = csub(a, c);
+        }
+        exch(v, s, t, T);
+        Ns = 2;
+    } else if (B == 4) {
+        // two radix-4 butterflies j = t + qT: inputs v[q + 2r]; outputs y[4j + r]
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            C a0 = v[q], a1 = v[q + 2], a2 = v[q + 4], a3 = v[q + 6];
+            dft4(a0, a1, a2, a3, inv);
+            const int j = t + q * T;
+            s[pad8(4 * j)] = a0;
+            s[pad8(4 * j + 1)] = a1;
+            s[pad8(4 * j + 2)] = a2;
+            s[pad8(4 * j + 3)] = a3;
+        }
+        exch(v, s, t, T);
+        Ns = 4;
+    }
+    constexpr int NST = LOGP / 3;          // radix-8 stages
+#pragma unroll
+    for (int st = 0; st < NST; ++st) {
+        const int k = t & (Ns - 1);
+        if (Ns > 1) {
+            const int m = k * ((P >> 3) / Ns) * twstep;
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twiddle(tw, r * m, inv));
+        }
+        dft8(v, inv);
+        if (st == NST - 1) break;
+        const int base = (t - k) * 8 + k;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) s[pad8(base + r * Ns)] = v[r];
+        exch(v, s, t, T);
+        Ns *= 8;
+    }
+}
+
 }  // namespace lsw

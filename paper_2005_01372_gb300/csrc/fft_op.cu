@@ -163,6 +163,145 @@ k_pass_c(const typename Cx<R>::T* __restrict__ T, DevGeom geo, int pz, int logpz
     }
 }
 
+// ------------------------------------------------- register-FFT passes
+// The same three passes with register-resident radix-8 line FFTs, for
+// 8 <= 2bz, 2bx <= 2048.  Here T holds, per field, bx columns of 2bz
+// entries: T[ix][kz].  Passes A and C read and write whole columns
+// (coalesced); pass B moves tiles of lpc rows through shared memory.
+template <typename R, int LOGP>
+__global__ void __launch_bounds__(256)
+k_fa(const typename Cx<R>::T* __restrict__ u, DevGeom geo, const typename Cx<R>::T* __restrict__ tw,
+     int twstep, int adjoint, typename Cx<R>::T* __restrict__ T) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int pz = 1 << LOGP, Tz = pz >> 3, lpc = 256 / Tz;
+    const int l = threadIdx.x / Tz, t = threadIdx.x - l * Tz;
+    C* s = reinterpret_cast<C*>(sm_raw) + l * (pad8(pz) + 1);
+    const int b = blockIdx.y;
+    const int ix = blockIdx.x * lpc + l;
+    const bool valid = ix < geo.bx;
+    const int2 org = box_origin(geo, b);
+    const C* ub = u + (long long)b * geo.bz * geo.bx + (long long)ix * geo.bz;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int iz = t + r * Tz;
+        C x = czero<C>();
+        if (valid && iz < geo.bz) {
+            x = ub[iz];
+            if (adjoint) {
+                x.y = -x.y;
+            } else {
+                const R ch = (R)geo.chi[(long long)(org.y + ix) * geo.chi_ld + org.x + iz];
+                x = cscale(x, ch);
+            }
+        }
+        v[r] = x;
+    }
+    fft_line<C, LOGP>(v, s, t, tw, twstep, false);
+    if (valid) {
+        C* Tb = T + (long long)b * pz * geo.bx + (long long)ix * pz;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) Tb[t + r * Tz] = v[r];
+    }
+}
+
+template <typename R, int LOGP>
+__global__ void __launch_bounds__(256)
+k_fb(typename Cx<R>::T* __restrict__ T, int pz, const typename Cx<R>::T* __restrict__ spt,
+     const typename Cx<R>::T* __restrict__ tw, int twstep) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int px = 1 << LOGP, bx = px >> 1, Tx = px >> 3, lpc = 256 / Tx;
+    constexpr int TS = bx + 4;                                   // tile row stride: conflict-free transposes
+    const int l = threadIdx.x / Tx, t = threadIdx.x - l * Tx;
+    C* tile = reinterpret_cast<C*>(sm_raw);                      // lpc rows of bx
+    C* s = tile + lpc * TS + l * (pad8(px) + 1);
+    const int b = blockIdx.y;
+    const int kz0 = blockIdx.x * lpc;
+    const int nrow = min(lpc, pz - kz0);
+    C* Tb = T + (long long)b * pz * bx;
+    for (int e = threadIdx.x; e < lpc * bx; e += 256) {
+        const int r = e % lpc, ix = e / lpc;
+        tile[r * TS + ix] = r < nrow ? Tb[(long long)ix * pz + kz0 + r] : czero<C>();
+    }
+    __syncthreads();
+    const int kz = kz0 + l;
+    C v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int kx = t + q * Tx;
+        v[q] = kx < bx ? tile[l * TS + kx] : czero<C>();
+    }
+    fft_line<C, LOGP>(v, s, t, tw, twstep, false);
+    const int qzz = kz < pz ? min(kz, pz - kz) : 0;     // rows past pz are padding
+    const C* sp = spt + (long long)qzz * (bx + 1);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int kx = t + q * Tx;
+        v[q] = cmul(v[q], sp[min(kx, px - kx)]);
+    }
+    fft_line<C, LOGP>(v, s, t, tw, twstep, true);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int kx = t + q * Tx;
+        if (kx < bx) tile[l * TS + kx] = v[q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < lpc * bx; e += 256) {
+        const int r = e % lpc, ix = e / lpc;
+        if (r < nrow) Tb[(long long)ix * pz + kz0 + r] = tile[r * TS + ix];
+    }
+}
+
+template <typename R, int LOGP>
+__global__ void __launch_bounds__(256)
+k_fc(const typename Cx<R>::T* __restrict__ T, DevGeom geo, const typename Cx<R>::T* __restrict__ tw,
+     int twstep, int mode, const typename Cx<R>::T* __restrict__ u, const typename Cx<R>::T* __restrict__ u0,
+     typename Cx<R>::T* __restrict__ y) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int pz = 1 << LOGP, Tz = pz >> 3, lpc = 256 / Tz;
+    const int l = threadIdx.x / Tz, t = threadIdx.x - l * Tz;
+    C* s = reinterpret_cast<C*>(sm_raw) + l * (pad8(pz) + 1);
+    const int b = blockIdx.y;
+    const int ix = blockIdx.x * lpc + l;
+    const bool valid = ix < geo.bx;
+    const C* Tb = T + (long long)b * pz * geo.bx + (long long)ix * pz;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = valid ? Tb[t + r * Tz] : czero<C>();
+    fft_line<C, LOGP>(v, s, t, tw, twstep, true);
+    if (!valid) return;
+    const int2 org = box_origin(geo, b);
+    const long long base = (long long)b * geo.bz * geo.bx + (long long)ix * geo.bz;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int iz = t + r * Tz;
+        if (iz >= geo.bz) continue;
+        const long long idx = base + iz;
+        const C g = v[r];
+        C out;
+        switch (mode) {
+            case LSW_OP_FORWARD:
+                out = u0 ? cadd(u0[idx], g) : g;
+                break;
+            case LSW_OP_RESIDUAL:
+                out = csub(u[idx], g);
+                if (u0) out = csub(out, u0[idx]);
+                break;
+            case LSW_OP_ADJOINT: {
+                const R ch = (R)geo.chi[(long long)(org.y + ix) * geo.chi_ld + org.x + iz];
+                out = mk(g.x * ch, -g.y * ch);
+                break;
+            }
+            default:
+                out = g;
+        }
+        y[idx] = out;
+    }
+}
+
 // ------------------------------------------------ generic strided 1D FFTs
 // nlines lines of length P: element i of line l at data[l * lstep + i * estep].
 template <int NT>
@@ -221,15 +360,20 @@ __global__ void k_extend(const double2* __restrict__ table, int nz, int bz, int 
     }
 }
 
-__global__ void k_quarter(const double2* __restrict__ F, int bz, int bx, double2* q64, float2* q32) {
+__global__ void k_quarter(const double2* __restrict__ F, int bz, int bx, double2* q64, float2* q32, double2* t64,
+                          float2* t32) {
     const int pz = 2 * bz;
     const int n = (bz + 1) * (bx + 1);
     const double sc = 1.0 / (4.0 * bz * bx);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int qx = e / (bz + 1), qz = e - qx * (bz + 1);
         const double2 v = F[(long long)qx * pz + qz];
-        q64[e] = make_double2(v.x * sc, v.y * sc);
-        q32[e] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+        const double2 w = make_double2(v.x * sc, v.y * sc);
+        const float2 f = make_float2((float)w.x, (float)w.y);
+        q64[e] = w;
+        q32[e] = f;
+        t64[qz * (bx + 1) + qx] = w;
+        t32[qz * (bx + 1) + qx] = f;
     }
 }
 
@@ -266,12 +410,75 @@ __global__ void k_point_sources(const double2* __restrict__ table, int nz, int n
     }
 }
 
+inline size_t pad8h(int i) { return (size_t)i + (size_t)(i >> 3); }
+
 int grid_for(long long n, int bs = 256) {
     long long g = (n + bs - 1) / bs;
     return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
 }
 
 }  // namespace
+
+// Launch the register-FFT passes for a runtime log2 size (3..11).
+template <typename K>
+lsw_status set_smem(K k, bool& done) {
+    if (!done) {
+        LSW_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        done = true;
+    }
+    return LSW_OK;
+}
+
+#define LSW_LOG_SWITCH(lg, ...)                  \
+    switch (lg) {                                \
+        case 3: { constexpr int L_ = 3; __VA_ARGS__; break; }   \
+        case 4: { constexpr int L_ = 4; __VA_ARGS__; break; }   \
+        case 5: { constexpr int L_ = 5; __VA_ARGS__; break; }   \
+        case 6: { constexpr int L_ = 6; __VA_ARGS__; break; }   \
+        case 7: { constexpr int L_ = 7; __VA_ARGS__; break; }   \
+        case 8: { constexpr int L_ = 8; __VA_ARGS__; break; }   \
+        case 9: { constexpr int L_ = 9; __VA_ARGS__; break; }   \
+        case 10: { constexpr int L_ = 10; __VA_ARGS__; break; } \
+        case 11: { constexpr int L_ = 11; __VA_ARGS__; break; } \
+        default: return LSW_ERR_UNSUPPORTED_SIZE;        \
+    }
+
+template <typename R>
+lsw_status launch_fa(int lg, dim3 grid, size_t sm, cudaStream_t st, const typename Cx<R>::T* u, DevGeom dg,
+                     const typename Cx<R>::T* tw, int tws, int adj, typename Cx<R>::T* work) {
+    static bool done[12] = {};
+    LSW_LOG_SWITCH(lg, {
+        LSW_TRY(set_smem(k_fa<R, L_>, done[L_]));
+        k_fa<R, L_><<<grid, 256, sm, st>>>(u, dg, tw, tws, adj, work);
+        LSW_LAUNCH_CHECK();
+    })
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status launch_fb(int lg, dim3 grid, size_t sm, cudaStream_t st, typename Cx<R>::T* work, int pz,
+                     const typename Cx<R>::T* spt, const typename Cx<R>::T* tw, int tws) {
+    static bool done[12] = {};
+    LSW_LOG_SWITCH(lg, {
+        LSW_TRY(set_smem(k_fb<R, L_>, done[L_]));
+        k_fb<R, L_><<<grid, 256, sm, st>>>(work, pz, spt, tw, tws);
+        LSW_LAUNCH_CHECK();
+    })
+    return LSW_OK;
+}
+
+template <typename R>
+lsw_status launch_fc(int lg, dim3 grid, size_t sm, cudaStream_t st, const typename Cx<R>::T* work, DevGeom dg,
+                     const typename Cx<R>::T* tw, int tws, int mode, const typename Cx<R>::T* u,
+                     const typename Cx<R>::T* u0, typename Cx<R>::T* y) {
+    static bool done[12] = {};
+    LSW_LOG_SWITCH(lg, {
+        LSW_TRY(set_smem(k_fc<R, L_>, done[L_]));
+        k_fc<R, L_><<<grid, 256, sm, st>>>(work, dg, tw, tws, mode, u, u0, y);
+        LSW_LAUNCH_CHECK();
+    })
+    return LSW_OK;
+}
 
 // ------------------------------------------------------------ op_apply
 template <typename R>
@@ -290,6 +497,18 @@ lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, i
 
     DevGeom dg{bz, bx, ilog2(bz), geo.chi, geo.chi_ld, geo.origin, geo.vpb > 0 ? geo.vpb : 1};
     const int logpz = ilog2(pz), logpx = ilog2(px);
+    if (pz >= 8 && px >= 8 && pz <= 2048 && px <= 2048 && sp.t32 && sp.t64) {
+        const C* spt = reinterpret_cast<const C*>(sizeof(R) == 8 ? (const void*)sp.t64 : (const void*)sp.t32);
+        const int lz = 256 / (pz >> 3), lx = 256 / (px >> 3);
+        const size_t smA = sizeof(C) * (size_t)lz * (pad8h(pz) + 1);
+        const size_t smB = sizeof(C) * ((size_t)lx * (bx + 4) + (size_t)lx * (pad8h(px) + 1));
+        const int twz = g->twP / pz, twx = g->twP / px;
+        dim3 gA((bx + lz - 1) / lz, nbatch), gB((pz + lx - 1) / lx, nbatch);
+        LSW_TRY(launch_fa<R>(logpz, gA, smA, st, u, dg, tw, twz, mode == LSW_OP_ADJOINT, work));
+        LSW_TRY(launch_fb<R>(logpx, gB, smB, st, work, pz, spt, tw, twx));
+        LSW_TRY(launch_fc<R>(logpz, gA, smA, st, work, dg, tw, twz, mode, u, u0, y));
+        return LSW_OK;
+    }
     // columns per CTA for passes A and C, rows per CTA for pass B
     int cx = std::min(bx, std::max(1, CAP / pz));
     cx = std::min(cx, 16);
@@ -356,12 +575,12 @@ lsw_status build_spectrum(const lsw_green* g, int bz, int bx, Spectrum* out, cud
     s.bz = bz;
     s.bx = bx;
     const size_t nq = (size_t)(bz + 1) * (bx + 1);
-    LSW_CUDA(cudaMalloc(&s.q64, nq * sizeof(double2)));
-    if (cudaMalloc(&s.q32, nq * sizeof(float2)) != cudaSuccess) {
-        cudaFree(s.q64);
+    if (cudaMalloc(&s.q64, nq * sizeof(double2)) != cudaSuccess || cudaMalloc(&s.q32, nq * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&s.t64, nq * sizeof(double2)) != cudaSuccess || cudaMalloc(&s.t32, nq * sizeof(float2)) != cudaSuccess) {
+        free_spectrum(&s);
         return LSW_ERR_OOM;
     }
-    k_quarter<<<grid_for((long long)nq), 256, 0, st>>>(E, bz, bx, s.q64, s.q32);
+    k_quarter<<<grid_for((long long)nq), 256, 0, st>>>(E, bz, bx, s.q64, s.q32, s.t64, s.t32);
     LSW_LAUNCH_CHECK();
     *out = s;
     return LSW_OK;
@@ -370,8 +589,12 @@ lsw_status build_spectrum(const lsw_green* g, int bz, int bx, Spectrum* out, cud
 void free_spectrum(Spectrum* s) {
     if (s->q64) cudaFree(s->q64);
     if (s->q32) cudaFree(s->q32);
+    if (s->t64) cudaFree(s->t64);
+    if (s->t32) cudaFree(s->t32);
     s->q64 = nullptr;
     s->q32 = nullptr;
+    s->t64 = nullptr;
+    s->t32 = nullptr;
 }
 
 lsw_status green_init(lsw_green* g, cudaStream_t st) {

@@ -29,7 +29,7 @@ template <typename C> __device__ __forceinline__ C ldop(const C* p, bool conj_) 
 // thread, K in steps of 8.  blockIdx.z = batch * ksplit + kpart; with
 // ksplit > 1 the partial products go to P (ksplit x batch x m x n) and a
 // second kernel reduces them in a fixed order.
-constexpr int GBK = 8;
+constexpr int GBK = 16;
 
 template <typename C, int BM, int BN>
 __global__ void __launch_bounds__(256)
@@ -38,6 +38,7 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
        int ksplit, int kchunk, C* __restrict__ P) {
     static_assert((BM / 4) * (BN / 4) == 256, "256 threads of 4 x 4 outputs");
     constexpr int TX = BN / 4, TY = BM / 4;
+    constexpr int NA = BM * GBK / 256, NB = GBK * BN / 256;
     __shared__ C As[GBK][BM + 1];
     __shared__ C Bs[GBK][BN + 1];
     const int bz = blockIdx.z;
@@ -52,24 +53,51 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = czero<C>();
-    for (int kk = kbeg; kk < kend; kk += GBK) {
-        for (int e = threadIdx.x; e < BM * GBK; e += 256) {
+    C ra[NA], rb[NB];
+    // tile loads into registers (element (i, t) of A's tile, (t, j) of B's)
+    auto load = [&](int kk) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int e = threadIdx.x + 256 * q;
             int i, t;
             if (opA == 0) { i = e % BM; t = e / BM; } else { t = e % GBK; i = e / GBK; }
             const int gi = i0 + i, gk = kk + t;
             C v = czero<C>();
             if (gi < m && gk < kend) v = opA == 0 ? Ab[(long long)gk * lda + gi] : ldop(Ab + (long long)gi * lda + gk, true);
-            As[t][i] = v;
+            ra[q] = v;
         }
-        for (int e = threadIdx.x; e < GBK * BN; e += 256) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = threadIdx.x + 256 * q;
             int t, j;
             if (opB == 0) { t = e % GBK; j = e / GBK; } else { j = e % BN; t = e / BN; }
             const int gj = j0 + j, gk = kk + t;
             C v = czero<C>();
             if (gj < n && gk < kend) v = opB == 0 ? Bb[(long long)gj * ldb + gk] : ldop(Bb + (long long)gk * ldb + gj, true);
-            Bs[t][j] = v;
+            rb[q] = v;
         }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            const int e = threadIdx.x + 256 * q;
+            int i, t;
+            if (opA == 0) { i = e % BM; t = e / BM; } else { t = e % GBK; i = e / GBK; }
+            As[t][i] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int e = threadIdx.x + 256 * q;
+            int t, j;
+            if (opB == 0) { t = e % GBK; j = e / GBK; } else { j = e % BN; t = e / BN; }
+            Bs[t][j] = rb[q];
+        }
+    };
+    if (kbeg < kend) load(kbeg);
+    for (int kk = kbeg; kk < kend; kk += GBK) {
+        store();
         __syncthreads();
+        if (kk + GBK < kend) load(kk + GBK);    // next tile in flight during the products
 #pragma unroll
         for (int t = 0; t < GBK; ++t) {
             C a[4], bb[4];
@@ -152,6 +180,42 @@ k_gemm_cn_small(int m, int n, int k, const C* __restrict__ A, int lda, long long
     }
 }
 
+// C = A^H B partial sums for tiny outputs (n <= 4 columns of B): warp w of
+// the CTA takes columns i = w, w + 8, ... of A and sums conj(A[r][i]) B[r][j]
+// over the CTA's rows with its 32 lanes striding the rows (coalesced), so
+// a thread keeps only n accumulators.
+template <typename C, int NN>
+__global__ void __launch_bounds__(256)
+k_gemm_cn_tiny(int m, int k, const C* __restrict__ A, int lda, long long sA, const C* __restrict__ B, int ldb,
+               long long sB, int kchunk, C* __restrict__ P, int batch) {
+    const int kp = blockIdx.x, b = blockIdx.y;
+    const int k0 = kp * kchunk, k1 = min(k, k0 + kchunk);
+    const C* Ab = A + b * sA;
+    const C* Bb = B + b * sB;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = w; i < m; i += 8) {
+        C acc[NN];
+#pragma unroll
+        for (int j = 0; j < NN; ++j) acc[j] = czero<C>();
+        const C* a = Ab + (long long)i * lda;
+#pragma unroll 4
+        for (int r = k0 + l; r < k1; r += 32) {
+            const C av = a[r];
+#pragma unroll
+            for (int j = 0; j < NN; ++j) cfmac(acc[j], av, Bb[(long long)j * ldb + r]);
+        }
+#pragma unroll
+        for (int j = 0; j < NN; ++j) {
+            C v = acc[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            }
+            if (l == 0) P[(((long long)kp * batch + b) * NN + j) * m + i] = v;
+        }
+    }
+}
+
 // C = alpha A B + beta C with a small inner dimension (k <= 64) and n <= 64:
 // B (k x n) sits in shared memory, thread (row, group of 16 columns) streams
 // its row of A.
@@ -180,6 +244,7 @@ k_gemm_nn_smallk(int m, int n, int k, C alpha, const C* __restrict__ A, int lda,
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
     const int j0 = g * 16;
+#pragma unroll 4
     for (int t = 0; t < k; ++t) {
         const C a = Ab[(long long)t * lda + i];
 #pragma unroll
@@ -1082,6 +1147,26 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
         const CT zero = czero<CT>();
         k_gemm<CT, 64, 64><<<dim3((m + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(
             oa, ob, m, n, 0, zero, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 1, 0, nullptr);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    // long inner products with a tiny result (Gram-Schmidt coefficients)
+    if (oa == 1 && ob == 0 && n <= 4 && m * n <= 32 && k >= 128) {
+        const long long want = std::max<long long>(1, 4864 / batch);
+        const int kchunk = (int)std::max<long long>(512, ((k + want - 1) / want + 255) / 256 * 256);
+        const int ksplit = (k + kchunk - 1) / kchunk;
+        DevBuf part;
+        LSW_TRY(part.alloc(sizeof(CT) * (size_t)ksplit * batch * m * n, st));
+        const dim3 gr(ksplit, batch);
+        switch (n) {
+            case 1: k_gemm_cn_tiny<CT, 1><<<gr, 256, 0, st>>>(m, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(), batch); break;
+            case 2: k_gemm_cn_tiny<CT, 2><<<gr, 256, 0, st>>>(m, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(), batch); break;
+            case 3: k_gemm_cn_tiny<CT, 3><<<gr, 256, 0, st>>>(m, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(), batch); break;
+            default: k_gemm_cn_tiny<CT, 4><<<gr, 256, 0, st>>>(m, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(), batch); break;
+        }
+        LSW_LAUNCH_CHECK();
+        k_gemm_reduce<CT><<<grid_for((long long)batch * m * n), 256, 0, st>>>(m, n, batch, ksplit, part.as<CT>(), alpha,
+                                                                              beta, C, ldc, sC);
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }

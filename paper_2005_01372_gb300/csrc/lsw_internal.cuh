@@ -98,6 +98,8 @@ struct Spectrum {
     int bz = 0, bx = 0;
     double2* q64 = nullptr;
     float2* q32 = nullptr;
+    double2* t64 = nullptr;   // the same quarter, kz-major: (bz + 1) x (bx + 1)
+    float2* t32 = nullptr;
 };
 
 }  // namespace lsw
