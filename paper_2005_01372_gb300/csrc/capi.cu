@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <mutex>
 #include <new>
 
 #include "lsw_internal.cuh"
@@ -18,6 +19,53 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+namespace {
+constexpr int kPool = 8;
+std::mutex g_pool_mu;
+cudaStream_t g_pool[64][kPool] = {};
+}  // namespace
+
+Fork::Fork(cudaStream_t parent) : parent_(parent) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        for (int i = 0; i < kPool; ++i) {
+            if (dev >= 0 && dev < 64 && !g_pool[dev][i]) cudaStreamCreateWithFlags(&g_pool[dev][i], cudaStreamNonBlocking);
+            streams_[i] = (dev >= 0 && dev < 64) ? g_pool[dev][i] : parent;
+        }
+    }
+    cudaEventCreateWithFlags(&start_, cudaEventDisableTiming);
+    cudaEventRecord(start_, parent_);
+}
+
+Fork::~Fork() {
+    if (used_) join();
+    if (start_) cudaEventDestroy(start_);
+}
+
+cudaStream_t Fork::child(int i) {
+    const int k = i % kPool;
+    if (!(used_ & (1u << k))) {
+        cudaStreamWaitEvent(streams_[k], start_, 0);
+        used_ |= 1u << k;
+    }
+    return streams_[k];
+}
+
+lsw_status Fork::join() {
+    for (int k = 0; k < kPool; ++k) {
+        if (!(used_ & (1u << k))) continue;
+        cudaEvent_t e;
+        LSW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        LSW_CUDA(cudaEventRecord(e, streams_[k]));
+        LSW_CUDA(cudaStreamWaitEvent(parent_, e, 0));
+        cudaEventDestroy(e);
+    }
+    used_ = 0;
+    return LSW_OK;
 }
 
 lsw_status green_init(lsw_green* g, cudaStream_t st);

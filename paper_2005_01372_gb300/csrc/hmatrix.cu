@@ -364,15 +364,12 @@ lsw_status range_finder(int ns, int nt, int rp, int q, int nblk, typename Cx<R>:
 // -(G0 V)[node c, node c^1], sketched on the box of the parent node.
 template <typename R>
 lsw_status build_level(const lsw_green* g, const double* chi, const Tree& tr, int l, int r, int rp, int q,
-                       uint64_t seed, HStore<R>& H, cudaStream_t st) {
+                       uint64_t seed, HStore<R>& H, const Spectrum& sp, cudaStream_t st) {
     typedef typename Cx<R>::T C;
     const int nblk = 1 << l, npar = 1 << (l - 1), nb = tr.nl(l);
     const int4 P0 = tr.node(l - 1, 0);
     const int bz = P0.y - P0.x, bx = P0.w - P0.z;
     const long long boxn = (long long)bz * bx;
-    Spectrum sp;
-    LSW_TRY(build_spectrum(g, bz, bx, &sp, st));
-    struct SpGuard { Spectrum* s; ~SpGuard() { free_spectrum(s); } } guard{&sp};
 
     std::vector<int> maps = tr.child_map(l, 0);
     std::vector<int> m1 = tr.child_map(l, 1);
@@ -423,7 +420,6 @@ lsw_status build_level(const lsw_green* g, const double* chi, const Tree& tr, in
     LSW_TRY((range_finder<R>(nb, nb, rp, q, nblk, om.as<C>(), qb.as<C>(), yt.as<C>(), fwd, adj, st)));
     LSW_TRY(truncate<R>(qb.as<C>(), nb, yt.as<C>(), nb, rp, r, nblk, minus_one<C>(), H.U[l], (long long)nb * r, H.W[l],
                         (long long)nb * r, st));
-    LSW_CUDA(cudaStreamSynchronize(st));   // the spectrum guard frees on return
     return LSW_OK;
 }
 
@@ -483,8 +479,9 @@ lsw_status hmv_adj(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X,
 // back to rank r by Algorithm 1 (q = 0) through its factors.
 template <typename R>
 lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, const typename Cx<R>::T* Y, int op,
-                       int call_l, int call_c, int oversample, uint64_t seed, cudaStream_t st,
+                       int call_l, int call_c, int oversample, uint64_t seed, cudaStream_t st0,
                        LeafUpd<R>* lu = nullptr) {
+    cudaStream_t st = st0;
     typedef typename Cx<R>::T C;
     const int m = M.nl(l), L = M.L, r = M.r, nL = M.nl(L);
     const int rp = r + oversample;
@@ -501,7 +498,10 @@ lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, c
         LSW_TRY(gemm<R>('N', 'C', nL, nL, r, one<C>(), X, m, nL, Y, m, nL, one<C>(), D0, nL, (long long)nL * nL, nleaf,
                         st));
     }
+    Fork fk(st0);
     for (int lp = l + 1; lp <= L; ++lp) {
+        // the levels' recompressions are independent of each other
+        cudaStream_t st = fk.child(lp);
         const int cnt = 1 << (lp - l), nb = M.nl(lp);
         const size_t first = (size_t)c * cnt;
         C* U0 = M.U[lp] + first * nb * r;
@@ -537,7 +537,7 @@ lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, c
         LSW_TRY(truncate<R>(ys.as<C>(), nb, yt.as<C>(), nb, rp, r, cnt, one<C>(), U0, (long long)nb * r, W0,
                             (long long)nb * r, st));
     }
-    return LSW_OK;
+    return fk.join();
 }
 
 // Inverse of node (l, c) of X written into the same node of Hi (recursive
@@ -631,7 +631,23 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
     HStore<R> X;
     struct Rel { HStore<R>* s; ~Rel() { s->release(); } } rel{&X};
     LSW_TRY(X.alloc(L, r, tr.n));
-    for (int l = 1; l <= L; ++l) LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, st));
+    // one spectrum per level (the parent boxes of a level share one shape)
+    std::vector<Spectrum> spec(L + 1);
+    struct SpecGuard {
+        std::vector<Spectrum>* v;
+        ~SpecGuard() { for (auto& s : *v) free_spectrum(&s); }
+    } specguard{&spec};
+    for (int l = 1; l <= L; ++l) {
+        const int4 P0 = tr.node(l - 1, 0);
+        LSW_TRY(build_spectrum(g, P0.y - P0.x, P0.w - P0.z, &spec[l], st));
+    }
+    {
+        // the levels are independent: sketch them concurrently
+        Fork fk(st);
+        for (int l = 1; l <= L; ++l)
+            LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, spec[l], fk.child(l)));
+        LSW_TRY(fk.join());
+    }
     const int nL = tr.nl(L);
     k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, st>>>(g->table, g->nz, chi, h->perm_d, nL, 1 << L, X.D);
     LSW_LAUNCH_CHECK();

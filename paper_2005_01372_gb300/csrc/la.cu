@@ -607,7 +607,9 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
         V[e] = mk((R)((e % k) == (e / k) ? 1 : 0), (R)0);
     }
     __syncthreads();
-    const R tol = sizeof(R) == 8 ? (R)1e-30 : (R)1e-13;
+    // squared off-diagonal norm relative to the total that the precision
+    // can reach (FP32 rounding stalls near 1e-13): stop there
+    const R tol = sizeof(R) == 8 ? (R)1e-26 : (R)1e-11;
     for (int sweep = 0; sweep < 40; ++sweep) {
         C part = czero<C>();
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
@@ -686,6 +688,121 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     __syncthreads();
     C* Vo = Vall + (long long)blockIdx.x * k * k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const int col = e / k, row = e - col * k;
+        Vo[e] = V[order[col] * k + row];
+    }
+}
+
+// The same Jacobi iteration with one warp per matrix (k <= 64) and several
+// matrices per CTA: lanes share the work of a round, __syncwarp orders it.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int batch) {
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int m = (k + 1) & ~1;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mat = blockIdx.x * (blockDim.x >> 5) + w;
+    const size_t per = sizeof(C) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2) + sizeof(int) * 64;
+    const size_t perA = (per + 15) & ~size_t(15);
+    unsigned char* base = sm_raw + perA * w;
+    C* A = reinterpret_cast<C*>(base);
+    C* V = A + k * k;
+    R* rot = reinterpret_cast<R*>(V + k * k);
+    int2* pr = reinterpret_cast<int2*>(rot + 4 * (m / 2));
+    int* order = reinterpret_cast<int*>(pr + m / 2);
+    if (mat >= batch) return;           // whole warp leaves together
+    const double2* G = Gall + (long long)mat * k * k;
+    double tr = 0;
+    for (int i = lane; i < k; i += 32) tr += fabs(G[i * k + i].x);
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    const double trs = tr > 0 ? 1.0 / tr : 0.0;
+    for (int e = lane; e < k * k; e += 32) {
+        A[e] = mk((R)(G[e].x * trs), (R)(G[e].y * trs));
+        V[e] = mk((R)((e % k) == (e / k) ? 1 : 0), (R)0);
+    }
+    __syncwarp();
+    // squared off-diagonal norm relative to the total that the precision
+    // can reach (FP32 rounding stalls near 1e-13): stop there
+    const R tol = sizeof(R) == 8 ? (R)1e-26 : (R)1e-11;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        R off = 0, tot = 0;
+        for (int e = lane; e < k * k; e += 32) {
+            const C a = A[e];
+            const R v = a.x * a.x + a.y * a.y;
+            tot += v;
+            if ((e % k) != (e / k)) off += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (!(off > tol * tot) || tot == 0) break;
+        for (int r = 0; r < m - 1; ++r) {
+            for (int i = lane; i < m / 2; i += 32) {
+                int p, q;
+                if (i == 0) { p = m - 1; q = r; }
+                else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
+                if (p > q) { const int t = p; p = q; q = t; }
+                R cs = 1, sn = 0, cp = 1, spp = 0;
+                if (q < k) {
+                    const R app = A[p * k + p].x, aqq = A[q * k + q].x;
+                    const C c = A[q * k + p];
+                    const R ac = sqrt(c.x * c.x + c.y * c.y);
+                    if (ac > (R)1e-30 * (fabs(app) + fabs(aqq)) && ac > 0) {
+                        const R tau = (aqq - app) / (2 * ac);
+                        const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+                        cs = (R)1 / sqrt((R)1 + t * t);
+                        sn = t * cs;
+                        cp = c.x / ac;
+                        spp = c.y / ac;
+                    }
+                }
+                rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
+                pr[i] = make_int2(p, q);
+            }
+            __syncwarp();
+            for (int e = lane; e < (m / 2) * k; e += 32) {
+                const int i = e / k, row = e - i * k;
+                const int p = pr[i].x, q = pr[i].y;
+                if (q >= k) continue;
+                const R cs = rot[4 * i], sn = rot[4 * i + 1];
+                const C em = mk(rot[4 * i + 2], -rot[4 * i + 3]);
+                for (int ww = 0; ww < 2; ++ww) {
+                    C* M = ww ? V : A;
+                    const C ap = M[p * k + row], aq = M[q * k + row];
+                    const C eq = cmul(em, aq);
+                    M[p * k + row] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
+                    M[q * k + row] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
+                }
+            }
+            __syncwarp();
+            for (int e = lane; e < (m / 2) * k; e += 32) {
+                const int i = e / k, col = e - i * k;
+                const int p = pr[i].x, q = pr[i].y;
+                if (q >= k) continue;
+                const R cs = rot[4 * i], sn = rot[4 * i + 1];
+                const C ep = mk(rot[4 * i + 2], rot[4 * i + 3]);
+                const C ap = A[col * k + p], aq = A[col * k + q];
+                const C eq = cmul(ep, aq);
+                A[col * k + p] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
+                A[col * k + q] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        for (int i = 0; i < k; ++i) order[i] = i;
+        for (int i = 0; i < k; ++i) {
+            int best = i;
+            for (int j = i + 1; j < k; ++j)
+                if (A[order[j] * k + order[j]].x > A[order[best] * k + order[best]].x) best = j;
+            const int t = order[i]; order[i] = order[best]; order[best] = t;
+        }
+    }
+    __syncwarp();
+    C* Vo = Vall + (long long)mat * k * k;
+    for (int e = lane; e < k * k; e += 32) {
         const int col = e / k, row = e - col * k;
         Vo[e] = V[order[col] * k + row];
     }
@@ -1301,13 +1418,27 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
     const int m = (k + 1) & ~1;
-    const size_t sm = sizeof(CT) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2);
+    const size_t per = sizeof(CT) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2) + sizeof(int) * 64;
+    const size_t perA = (per + 15) & ~size_t(15);
+    const int wpc = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perA));
     static bool attr[2] = {false, false};
     if (!attr[sizeof(R) == 8]) {
-        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi_warp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr[sizeof(R) == 8] = true;
     }
-    k_heev_jacobi<R><<<batch, 256, sm, st>>>(G, V, k);
+    if (batch >= 4 * 152) {
+        // many matrices: one warp each
+        k_heev_jacobi_warp<R><<<(batch + wpc - 1) / wpc, 32 * wpc, perA * wpc, st>>>(G, V, k, batch);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
+    }
+    static bool attrb[2] = {false, false};
+    if (!attrb[sizeof(R) == 8]) {
+        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attrb[sizeof(R) == 8] = true;
+    }
+    const size_t smb = sizeof(CT) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2);
+    k_heev_jacobi<R><<<batch, 256, smb, st>>>(G, V, k);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }

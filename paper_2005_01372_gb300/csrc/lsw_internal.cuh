@@ -90,6 +90,23 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Fork independent work from a parent stream onto library-owned streams and
+// join it back: child(i) starts after everything enqueued on the parent so
+// far; join() makes the parent wait for every child used.
+class Fork {
+  public:
+    explicit Fork(cudaStream_t parent);
+    ~Fork();
+    cudaStream_t child(int i);
+    lsw_status join();
+
+  private:
+    cudaStream_t parent_;
+    cudaEvent_t start_ = nullptr;
+    unsigned used_ = 0;
+    cudaStream_t streams_[8] = {};
+};
+
 // ------------------------------------------------------------ FFT geometry
 // One spectrum of a (bz x bx) box: the FFT of the even extension of the
 // Green table to (2bz x 2bx), scaled by 1/(4 bz bx), as its quarter
