@@ -102,6 +102,15 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+DOMINANT = "qr"
+
+
+def fp32_alu_peak_tflops() -> float:
+    """FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops
+    (fused multiply-add) x 2.07 GHz maximum SM clock."""
+    return round(152 * 128 * 2 * 2.07e9 / 1e12, 1)
+
+
 def op_bytes_c64(n: int, nsrc: int) -> float:
     """Algorithmic bytes of one batched c64 operator apply (RESIDUAL mode):
     read u and u0, write y (8 B each per cell and source), plus chi (8 B per
@@ -146,13 +155,17 @@ def run_ours(args):
         step(vel)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, inputs resident in HBM, L2 flushed between steps
+    # ---- timed region: K steps, inputs resident in HBM, L2 flushed between steps.
+    # The dominant kernel family (the row-chunk QR of the sketch blocks, by its
+    # share of the ncu launch list) is timed live with CUDA events on its
+    # launching stream.
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     l0 = lsw.launch_count()
+    lsw.kernel_timer_start(DOMINANT)
     times, conv, worst = [], 0, 0.0
     t_wall = time.perf_counter()
     for _ in range(args.steps):
@@ -169,6 +182,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     launches = lsw.launch_count() - l0
+    dom_ms, dom_bytes, dom_flops, dom_n = lsw.kernel_timer_read()
+    lsw.kernel_timer_stop()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -182,9 +197,11 @@ def run_ours(args):
     solves = float(c.item())
     value = solves / (ms_max / 1e3)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers; the FFT
+    # operator's three passes are timed live inside these solves
     e2e_times = []
     out_host = torch.empty((len(wl.sources), wl.n), dtype=torch.complex128).pin_memory()
+    lsw.kernel_timer_start("operator_c64")
     for _ in range(max(1, min(args.steps, 2))):
         flush.zero_()
         torch.cuda.synchronize()
@@ -196,36 +213,27 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
+    op_ms, op_bytes, op_flops, op_n = lsw.kernel_timer_read()
+    lsw.kernel_timer_stop()
     e2e_value = sum(1 for i in infos if i.status == 0 and i.rel_residual <= TOL) * world / (
         float(np.mean(e2e_times)) / 1e3)
 
-    # ---- FFT operator roofline: the batched c64 RESIDUAL apply of the solve
-    G = lsw.build_green(wl.nz, wl.nx, wl.h, wl.c0, wl.freq_hz)
-    chi = G.contrast(vel)
-    u0 = G.point_sources(wl.sources, lsw.C64)
-    uu = u0.clone()
-    yy = torch.empty_like(u0)
-    for _ in range(5):
-        lsw.apply_operator(G, chi, uu, u0, lsw.OP_RESIDUAL, y=yy)
-    reps = 50
-    big = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    op_ms = []
-    for _ in range(reps):
-        big.zero_()           # cold L2, like a call inside the solve loop after other work
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lsw.apply_operator(G, chi, uu, u0, lsw.OP_RESIDUAL, y=yy)
-        e1.record(stream)
-        e1.synchronize()
-        op_ms.append(e0.elapsed_time(e1))
-    op_avg = float(np.mean(op_ms))
-    algo = op_bytes_c64(wl.n, len(wl.sources))
     peak, peak_kind = load_peaks()
-    achieved = algo / (op_avg / 1e3) / 1e9
-    roof = {"kernel": "lsw_apply_operator c64 RESIDUAL, 32 fields (passes A+B+C)", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "algorithmic_bytes": algo,
-            "avg_launch_ms": round(op_avg, 4)}
+    fp32_peak = fp32_alu_peak_tflops()
+    dom_gbs = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    roof = {"kernel": "k_tsqr_chunk: row-chunk Householder QR of the sketch blocks (largest share of the step)",
+            "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": round(dom_gbs / peak, 4), "traffic": None, "launches": int(dom_n),
+            "avg_launch_ms": round(dom_ms / max(1, dom_n), 4),
+            "achieved_tflops": round(dom_flops / (dom_ms / 1e3) / 1e12, 3) if dom_ms > 0 else 0.0}
+    op_tf = op_flops / (op_ms / 1e3) / 1e12 if op_ms > 0 else 0.0
+    op_gbs = op_bytes / (op_ms / 1e3) / 1e9 if op_ms > 0 else 0.0
+    op_roof = {"kernel": "FFT operator in FP32, passes k_fa + k_fb + k_fc, timed inside the solves", "bound": "alu",
+               "achieved": round(op_tf, 2), "peak": fp32_peak,
+               "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+               "unit": "TFLOP/s", "frac": round(op_tf / fp32_peak, 4), "algorithmic_gbs": round(op_gbs, 1),
+               "hbm_frac": round(op_gbs / peak, 4), "applies": int(op_n),
+               "avg_apply_ms": round(op_ms / max(1, op_n), 4)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
@@ -238,7 +246,7 @@ def run_ours(args):
                            "solver": "FGMRES(30) right-preconditioned, FP64 iterative refinement to 1e-6",
                            "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas{world}"},
                 "solves_converged": int(solves), "max_rel_residual": worst,
-                "roofline": roof,
+                "roofline": roof, "operator_roofline": op_roof,
                 "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": int(vel_host.numel() * 8),
                         "d2h_bytes_per_step": int(out_host.numel() * 16)},
                 "clocks": clk, "gpu_launches": int(launches), "wall_s": round(wall, 3)}

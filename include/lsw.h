@@ -119,6 +119,19 @@ const char* lsw_last_error(void);
  * (diagnostics; every call's kernels are counted as they are enqueued). */
 uint64_t lsw_launch_count(void);
 
+/* Diagnostic timing of one kernel family inside any call (not part of the
+ * method).  lsw_kernel_timer_start(family) resets and enables it for
+ * "operator_c64" / "operator_c128" (the three FFT passes of one operator
+ * apply in that precision), "qr" (the row
+ * chunks of the tall-skinny QR) or "gj_update" (the Gauss-Jordan block
+ * updates); CUDA events are then recorded on the launching stream around
+ * each such launch, with the algorithmic bytes and flops of its work.
+ * lsw_kernel_timer_read waits for the recorded events and reports the sums
+ * (any pointer may be NULL). */
+lsw_status lsw_kernel_timer_start(const char* family);
+lsw_status lsw_kernel_timer_read(double* total_ms, double* bytes, double* flops, uint64_t* launches);
+lsw_status lsw_kernel_timer_stop(void);
+
 /* Green table and spectra (Sec. 2.2).
  * Tabulates the cell-integrated Green's function Gt at every offset
  * 0 <= dz <= nz, 0 <= dx <= nx in FP64 (Bessel J0, J1, Y0, Y1), builds its

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <utility>
+#include <vector>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -19,6 +21,49 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+namespace {
+struct TimerState {
+    std::mutex mu;
+    char family[64] = {0};
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0, bytes = 0, flops = 0;
+    unsigned long long launches = 0;
+} g_timer;
+
+void drain_timer() {
+    for (auto& pe : g_timer.pending) {
+        float t = 0;
+        cudaEventSynchronize(pe.second);
+        if (cudaEventElapsedTime(&t, pe.first, pe.second) == cudaSuccess) g_timer.ms += t;
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    g_timer.pending.clear();
+}
+}  // namespace
+
+KTimer::KTimer(const char* family, cudaStream_t st, double bytes, double flops) {
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    if (!g_timer.on || strncmp(family, g_timer.family, sizeof g_timer.family) != 0) return;
+    st_ = st;
+    bytes_ = bytes;
+    flops_ = flops;
+    cudaEventCreate(&e0_);
+    cudaEventCreate(&e1_);
+    cudaEventRecord(e0_, st_);
+}
+
+KTimer::~KTimer() {
+    if (!e0_) return;
+    cudaEventRecord(e1_, st_);
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    g_timer.pending.emplace_back(e0_, e1_);
+    g_timer.bytes += bytes_;
+    g_timer.flops += flops_;
+    g_timer.launches += 1;
 }
 
 namespace {
@@ -103,6 +148,34 @@ const char* lsw_status_string(lsw_status s) {
 const char* lsw_last_error(void) { return g_last_error; }
 
 uint64_t lsw_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+lsw_status lsw_kernel_timer_start(const char* family) {
+    if (!family) return LSW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    drain_timer();
+    strncpy(g_timer.family, family, sizeof g_timer.family - 1);
+    g_timer.on = true;
+    g_timer.ms = g_timer.bytes = g_timer.flops = 0;
+    g_timer.launches = 0;
+    return LSW_OK;
+}
+
+lsw_status lsw_kernel_timer_read(double* ms, double* bytes, double* flops, uint64_t* launches) {
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    drain_timer();
+    if (ms) *ms = g_timer.ms;
+    if (bytes) *bytes = g_timer.bytes;
+    if (flops) *flops = g_timer.flops;
+    if (launches) *launches = g_timer.launches;
+    return LSW_OK;
+}
+
+lsw_status lsw_kernel_timer_stop(void) {
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    drain_timer();
+    g_timer.on = false;
+    return LSW_OK;
+}
 
 lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out) {
     if (!grid || !out) return LSW_ERR_INVALID_ARG;

@@ -412,6 +412,20 @@ __global__ void k_point_sources(const double2* __restrict__ table, int nz, int n
 
 inline size_t pad8h(int i) { return (size_t)i + (size_t)(i >> 3); }
 
+// Algorithmic bytes of one batched apply: per field read u (and u0) and
+// write y; chi (FP64) and the quarter spectrum once per batch.
+double op_bytes(size_t elem, int bz, int bx, int nb, bool has_u0, int) {
+    const double cells = (double)bz * bx;
+    return (double)elem * cells * (2.0 + (has_u0 ? 1.0 : 0.0)) * nb + 8.0 * cells + (double)elem * (bz + 1) * (bx + 1);
+}
+// 5 N log2 N per complex FFT: nx columns of 2nz, 2nz rows forward and back
+// of 2nx, nx columns back; 6 per spectrum product.
+double op_flops(int bz, int bx, int nb) {
+    const double pz = 2.0 * bz, px = 2.0 * bx;
+    const double fz = 5.0 * pz * std::log2(pz), fx = 5.0 * px * std::log2(px);
+    return nb * (2.0 * bx * fz + 2.0 * pz * fx + 6.0 * pz * px);
+}
+
 int grid_for(long long n, int bs = 256) {
     long long g = (n + bs - 1) / bs;
     return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
@@ -504,6 +518,8 @@ lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, i
         const size_t smB = sizeof(C) * ((size_t)lx * (bx + 4) + (size_t)lx * (pad8h(px) + 1));
         const int twz = g->twP / pz, twx = g->twP / px;
         dim3 gA((bx + lz - 1) / lz, nbatch), gB((pz + lx - 1) / lx, nbatch);
+        KTimer kt(sizeof(R) == 8 ? "operator_c128" : "operator_c64", st, op_bytes(sizeof(C), bz, bx, nbatch, u0 != nullptr, mode),
+                  op_flops(bz, bx, nbatch));
         LSW_TRY(launch_fa<R>(logpz, gA, smA, st, u, dg, tw, twz, mode == LSW_OP_ADJOINT, work));
         LSW_TRY(launch_fb<R>(logpx, gB, smB, st, work, pz, spt, tw, twx));
         LSW_TRY(launch_fc<R>(logpz, gA, smA, st, work, dg, tw, twz, mode, u, u0, y));

@@ -374,95 +374,137 @@ __device__ __forceinline__ C block_sum(C v, C* red) {
     return s;
 }
 
-// Householder factorisation of A (m x k, ld m) in place, then the explicit
-// thin Q.  Rout (k x k, column-major), if given, receives R before Q
-// overwrites A.  Works on global or shared memory alike.
-// Sums of acc[0..nc) over the CTA (two barriers for all nc values); every
-// thread receives the sums in out[0..nc).
-template <typename C, int NT>
-__device__ __forceinline__ void block_sum16(const C* acc, int nc, C* red16 /* [NT/32][16] */, C* out) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+// Warp reduce-scatter: on entry every lane holds 32 values; on exit v[0]
+// of lane l is the sum over the warp of value l (31 shuffles per lane).
+template <typename C>
+__device__ __forceinline__ void warp_reduce_scatter32(C v[32]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        C v = acc[q];
-        for (int o = 16; o > 0; o >>= 1) {
-            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            const C send = upper ? v[i] : v[i + w];
+            const C keep = upper ? v[i + w] : v[i];
+            C recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, send.x, w);
+            recv.y = __shfl_xor_sync(0xffffffffu, send.y, w);
+            v[i] = cadd(keep, recv);
         }
-        if (l == 0 && q < nc) red16[w * 16 + q] = v;
     }
-    __syncthreads();
-    if (threadIdx.x < nc) {
-        C s = czero<C>();
-        for (int ww = 0; ww < NT / 32; ++ww) s = cadd(s, red16[ww * 16 + threadIdx.x]);
-        red16[(NT / 32) * 16 + threadIdx.x] = s;
-    }
-    __syncthreads();
-    for (int q = 0; q < nc; ++q) out[q] = red16[(NT / 32) * 16 + q];
 }
 
+// CTA sums of up to 32 values per thread: out[c] (shared) = sum over the
+// CTA of v[c].  Two barriers.
+template <typename C, int NT>
+__device__ __forceinline__ void cta_sum32(C v[32], C* red /* [NT/32][32] */, C* out /* [32] */) {
+    warp_reduce_scatter32(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    red[w * 32 + lane] = v[0];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        C s = czero<C>();
+#pragma unroll
+        for (int ww = 0; ww < NT / 32; ++ww) s = cadd(s, red[ww * 32 + threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Householder factorisation of A (m x k, ld m, k <= 64) in place, then the
+// explicit thin Q.  Rout (k x k, column-major), if given, receives R before
+// Q overwrites A.  Works on global or shared memory alike.
+//
+// Reflectors follow LAPACK's zlarfg convention: H = I - tau v v^H,
+// v = [1; s x] with s = 1 / (alpha - beta), H^H [alpha; x] = [beta; 0].
+// One pass over the rows below the diagonal gathers ||x||^2 and every
+// x^H a_c of the trailing columns together, since
+//     v^H a_c = a_c[j] + conj(s) x^H a_c[j+1:],
+// so each column costs one CTA reduction; each thread keeps the same rows
+// throughout, so the updates need no further barrier.
 template <typename R, int NT>
 __device__ void hh_qr(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* Rout) {
     typedef typename Cx<R>::T C;
-    __shared__ C red[33];
+    __shared__ C red[(NT / 32) * 32];
+    __shared__ C sums[32];
+    __shared__ C wv[64];          // the reflector's coefficients for the trailing columns
     __shared__ C tau_s[64];
-    __shared__ C red16[(NT / 32 + 1) * 16];
-    C wv[16];
+    __shared__ C hdr[3];          // tau, s, beta of the current column
     const int kk = min(k, m);
     // ---- factorisation
     for (int j = 0; j < kk; ++j) {
         C* aj = A + (long long)j * m;
-        C part = czero<C>();
-        for (int i = j + 1 + threadIdx.x; i < m; i += NT) part.x += aj[i].x * aj[i].x + aj[i].y * aj[i].y;
-        const R xnorm2 = block_sum<C, NT>(part, red).x;
-        const C alpha = aj[j];
-        C tau = czero<C>();
-        R beta = alpha.x;
-        const bool skip = (xnorm2 == 0 && alpha.y == 0);
-        if (!skip) {
-            const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
-            beta = alpha.x >= 0 ? -nrm : nrm;
-            tau = mk((beta - alpha.x) / beta, -alpha.y / beta);
-            const C d = mk(alpha.x - beta, alpha.y);       // scale x by 1 / (alpha - beta)
-            const R den = d.x * d.x + d.y * d.y;
-            const C sc = mk(d.x / den, -d.y / den);
-            for (int i = j + 1 + threadIdx.x; i < m; i += NT) aj[i] = cmul(aj[i], sc);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tau_s[j] = tau;
-            aj[j] = mk(beta, (R)0);
-        }
-        __syncthreads();
-        if (skip) continue;
-        // apply H^H = I - conj(tau) v v^H to columns j+1..k-1, 16 at a time
-        for (int c0 = j + 1; c0 < k; c0 += 16) {
-            const int nc = min(16, k - c0);
-            C acc[16];
+        // trailing columns in groups of 31 (slot 31 of the first group: ||x||^2)
+        for (int g0 = j + 1, first = 1; first || g0 < k; g0 += 31, first = 0) {
+            const int nc = min(31, k - g0);
+            C acc[32];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
-            for (int i = j + threadIdx.x; i < m; i += NT) {
-                const C v = i == j ? mk((R)1, (R)0) : aj[i];
+            for (int q = 0; q < 32; ++q) acc[q] = czero<C>();
+            for (int i = threadIdx.x; i < m; i += NT) {
+                if (i <= j) continue;
+                const C x = aj[i];
+                if (first) acc[31].x += x.x * x.x + x.y * x.y;
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (q < nc) cfmac(acc[q], v, A[(long long)(c0 + q) * m + i]);
+                for (int q = 0; q < 31; ++q)
+                    if (q < nc) cfmac(acc[q], x, A[(long long)(g0 + q) * m + i]);
             }
-            block_sum16<C, NT>(acc, nc, red16, wv);
-            for (int q = 0; q < nc; ++q) wv[q] = cmulc(tau, wv[q]);   // conj(tau) * (v^H a)
-            for (int i = j + threadIdx.x; i < m; i += NT) {
-                const C v = i == j ? mk((R)1, (R)0) : aj[i];
-                for (int q = 0; q < nc; ++q) {
-                    C* a = A + (long long)(c0 + q) * m + i;
-                    *a = csub(*a, cmul(v, wv[q]));
+            cta_sum32<C, NT>(acc, red, sums);
+            if (first && threadIdx.x == 0) {
+                const C alpha = aj[j];
+                const R xnorm2 = sums[31].x;
+                C tau = czero<C>(), scale = czero<C>();
+                R beta = alpha.x;
+                if (!(xnorm2 == 0 && alpha.y == 0)) {
+                    const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+                    beta = alpha.x >= 0 ? -nrm : nrm;
+                    tau = mk((beta - alpha.x) / beta, -alpha.y / beta);
+                    const C d = mk(alpha.x - beta, alpha.y);
+                    const R den = d.x * d.x + d.y * d.y;
+                    scale = mk(d.x / den, -d.y / den);
+                }
+                hdr[0] = tau;
+                hdr[1] = scale;
+                hdr[2] = mk(beta, (R)0);
+                tau_s[j] = tau;
+            }
+            if (first) __syncthreads();
+            // v^H a_c = a_c[j] + conj(s) (x^H a_c);  wv_c = conj(tau) v^H a_c
+            if (threadIdx.x < nc) {
+                const C ajc = A[(long long)(g0 + threadIdx.x) * m + j];
+                wv[g0 + threadIdx.x - j - 1] = cmulc(hdr[0], cadd(ajc, cmulc(hdr[1], sums[threadIdx.x])));
+            }
+            __syncthreads();   // wv complete, row j read by all before any update
+            if (nc <= 0) break;
+        }
+        const C tau = hdr[0], scale = hdr[1];
+        const R beta = hdr[2].x;
+        const bool skip = tau.x == 0 && tau.y == 0;
+        if (!skip) {
+            for (int i = threadIdx.x; i < m; i += NT) {
+                if (i < j) continue;
+                if (i == j) {
+                    for (int c = j + 1; c < k; ++c) {
+                        C* a = A + (long long)c * m + j;
+                        *a = csub(*a, wv[c - j - 1]);
+                    }
+                    continue;
+                }
+                const C v = cmul(aj[i], scale);
+                aj[i] = v;
+                for (int c = j + 1; c < k; ++c) {
+                    C* a = A + (long long)c * m + i;
+                    *a = csub(*a, cmul(v, wv[c - j - 1]));
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
+        if (threadIdx.x == 0) aj[j] = mk(beta, (R)0);
     }
+    __syncthreads();
     if (Rout) {
         for (int e = threadIdx.x; e < k * k; e += NT) {
-            const int j = e / k, i = e - j * k;
-            Rout[e] = (i <= j && i < kk) ? A[(long long)j * m + i] : czero<C>();
+            const int jj = e / k, i = e - jj * k;
+            Rout[e] = (i <= jj && i < kk) ? A[(long long)jj * m + i] : czero<C>();
         }
         __syncthreads();
     }
@@ -475,32 +517,32 @@ __device__ void hh_qr(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* Rou
             continue;
         }
         const C tau = tau_s[j];
-        for (int c0 = j + 1; c0 < k; c0 += 16) {
-            const int nc = min(16, k - c0);
-            C acc[16];
+        // w_c = tau v^H q_c = tau (q_c[j] + sum_{i>j} conj(v_i) q_c[i])
+        for (int g0 = j + 1; g0 < k; g0 += 32) {
+            const int nc = min(32, k - g0);
+            C acc[32];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
-            for (int i = j + threadIdx.x; i < m; i += NT) {
-                const C v = i == j ? mk((R)1, (R)0) : aj[i];
+            for (int q = 0; q < 32; ++q) acc[q] = czero<C>();
+            for (int i = threadIdx.x; i < m; i += NT) {
+                if (i <= j) continue;
+                const C v = aj[i];
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (q < nc) cfmac(acc[q], v, A[(long long)(c0 + q) * m + i]);
+                for (int q = 0; q < 32; ++q)
+                    if (q < nc) cfmac(acc[q], v, A[(long long)(g0 + q) * m + i]);
             }
-            block_sum16<C, NT>(acc, nc, red16, wv);
-            for (int q = 0; q < nc; ++q) wv[q] = cmul(tau, wv[q]);      // tau * (v^H a)
-            for (int i = j + threadIdx.x; i < m; i += NT) {
-                const C v = i == j ? mk((R)1, (R)0) : aj[i];
-                for (int q = 0; q < nc; ++q) {
-                    C* a = A + (long long)(c0 + q) * m + i;
-                    *a = csub(*a, cmul(v, wv[q]));
-                }
-            }
+            cta_sum32<C, NT>(acc, red, sums);
+            if (threadIdx.x < nc)
+                wv[g0 + threadIdx.x - j - 1] = cmul(tau, cadd(A[(long long)(g0 + threadIdx.x) * m + j], sums[threadIdx.x]));
             __syncthreads();
         }
         for (int i = threadIdx.x; i < m; i += NT) {
-            if (i < j) aj[i] = czero<C>();
-            else if (i == j) aj[i] = mk((R)1 - tau.x, -tau.y);
-            else aj[i] = mk(-(tau.x * aj[i].x - tau.y * aj[i].y), -(tau.x * aj[i].y + tau.y * aj[i].x));
+            if (i < j) { aj[i] = czero<C>(); continue; }
+            const C v = i == j ? mk((R)1, (R)0) : aj[i];
+            for (int c = j + 1; c < k; ++c) {
+                C* a = A + (long long)c * m + i;
+                *a = csub(*a, cmul(v, wv[c - j - 1]));
+            }
+            aj[i] = i == j ? mk((R)1 - tau.x, -tau.y) : mk(-(tau.x * v.x - tau.y * v.y), -(tau.x * v.y + tau.y * v.x));
         }
         __syncthreads();
     }
@@ -1364,7 +1406,7 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
     if (batch <= 0 || k <= 0 || m <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
     (void)work;
-    constexpr int NT = 256;
+    constexpr int NT = 512;
     const size_t cap = 200 * 1024;
     int cmax = (int)std::min<size_t>(1024, (cap / sizeof(CT) - (size_t)k * k) / k);
     static bool attr[2] = {false, false};
@@ -1381,6 +1423,8 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
     if (nch == 1) {
         DevBuf S;
         LSW_TRY(S.alloc(sizeof(CT) * (size_t)batch * k * k, st));
+        KTimer kt("qr", st, sizeof(CT) * ((double)batch * m * k * 2 + (double)batch * k * k),
+                  16.0 * batch * (double)m * k * k);
         k_tsqr_chunk<R, NT><<<dim3(1, batch), NT, smem, st>>>(A, m, k, sA, 1, S.as<CT>());
         LSW_LAUNCH_CHECK();
         return LSW_OK;
@@ -1388,8 +1432,14 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
     DevBuf S;
     const int ms = nch * k;
     LSW_TRY(S.alloc(sizeof(CT) * (size_t)batch * ms * k, st));
-    k_tsqr_chunk<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
-    LSW_LAUNCH_CHECK();
+    {
+        // reads and rewrites its rows, writes the R factors; Householder and
+        // explicit Q: 16 m k^2 real flops per block (8 each)
+        KTimer kt("qr", st, sizeof(CT) * ((double)batch * m * k * 2 + (double)batch * ms * k),
+                  16.0 * batch * (double)m * k * k);
+        k_tsqr_chunk<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
+        LSW_LAUNCH_CHECK();
+    }
     LSW_TRY(qr_explicit<R>(S.as<CT>(), ms, k, (long long)ms * k, batch, nullptr, st));
     k_tsqr_apply<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
     LSW_LAUNCH_CHECK();
@@ -1479,9 +1529,13 @@ lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cuda
             k_gj_panel_reg<CT, NT, NB><<<batch, NT, 0, st>>>(cur, n, sA, k0, w, piv.as<int>());
             LSW_LAUNCH_CHECK();
             if (w == n) continue;
-            k_gj_update_oop<CT><<<dim3((n + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(cur, nxt, n, sA, k0, w,
-                                                                                          piv.as<int>());
-            LSW_LAUNCH_CHECK();
+            {
+                // reads and writes every matrix once; 8 n^2 w real flops each
+                KTimer kt("gj_update", st, 2.0 * sizeof(CT) * (double)n * n * batch, 8.0 * (double)n * n * w * batch);
+                k_gj_update_oop<CT><<<dim3((n + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(cur, nxt, n, sA, k0, w,
+                                                                                              piv.as<int>());
+                LSW_LAUNCH_CHECK();
+            }
             std::swap(cur, nxt);
         }
         if (cur != A) {

@@ -67,6 +67,21 @@ template <typename C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
 void count_launch();
 
+// Diagnostic timing of one kernel family (lsw_kernel_timer_*): while the
+// family named at lsw_kernel_timer_start is enabled, a KTimer records CUDA
+// events on the launching stream around the launches it scopes and adds the
+// algorithmic bytes and flops its caller states.
+class KTimer {
+  public:
+    KTimer(const char* family, cudaStream_t st, double bytes, double flops);
+    ~KTimer();
+
+  private:
+    cudaEvent_t e0_ = nullptr, e1_ = nullptr;
+    cudaStream_t st_ = nullptr;
+    double bytes_ = 0, flops_ = 0;
+};
+
 inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
 

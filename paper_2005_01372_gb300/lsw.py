@@ -66,6 +66,10 @@ _SIGS = {
     "lsw_status_string": (ctypes.c_char_p, [I32]),
     "lsw_last_error": (ctypes.c_char_p, []),
     "lsw_launch_count": (ctypes.c_uint64, []),
+    "lsw_kernel_timer_start": (I32, [ctypes.c_char_p]),
+    "lsw_kernel_timer_read": (I32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+    "lsw_kernel_timer_stop": (I32, []),
     "lsw_build_green": (I32, [ctypes.POINTER(_Grid), VP, ctypes.POINTER(VP)]),
     "lsw_destroy_green": (I32, [VP]),
     "lsw_green_table": (I32, [VP, VP, VP]),
@@ -208,6 +212,25 @@ class Green:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(lib().lsw_launch_count())
+
+
+def kernel_timer_start(family: str):
+    """Time every launch of one kernel family ("operator_c64", "operator_c128",
+    "qr", "gj_update")
+    with CUDA events on its stream, from now on."""
+    _check(lib().lsw_kernel_timer_start(family.encode()), "lsw_kernel_timer_start")
+
+
+def kernel_timer_read():
+    """(total ms, algorithmic bytes, flops, launches) since kernel_timer_start."""
+    ms, by, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+    _check(lib().lsw_kernel_timer_read(ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl), ctypes.byref(n)),
+           "lsw_kernel_timer_read")
+    return ms.value, by.value, fl.value, n.value
+
+
+def kernel_timer_stop():
+    _check(lib().lsw_kernel_timer_stop(), "lsw_kernel_timer_stop")
 
 
 def build_green(nz, nx, h, c0, freq_hz, stream=None) -> Green:
