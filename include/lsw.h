@@ -242,6 +242,41 @@ lsw_status lsw_solve_series(const lsw_green* g, const double* chi, const lsw_hma
                             const void* u0, void* u, int nbatch, const lsw_solve_params* sp,
                             lsw_solve_info* info, void* stream);
 
+/* One (grid, frequency) problem of a batched solve. */
+typedef struct {
+    lsw_grid grid;
+    const double* velocity;   /* device, nz * nx velocities (strip order)         */
+    const int32_t* sources;   /* HOST, 2 * nsrc int32: (iz, ix) per point source  */
+    int32_t nsrc;
+    int32_t pad_;
+    void* u;                  /* device output, nsrc fields: complex128 for
+                                 LSW_C128 / LSW_MIXED, complex64 for LSW_C64      */
+} lsw_problem;
+
+/* Solve many (grid, frequency) problems.  The preconditioner of a problem
+ * serves all of its sources (Sec. 3: extra sources cost little once H is
+ * built).  For every problem: Green table and spectrum, contrast (Eq. 1),
+ * point sources, H from *hp (NULL: no preconditioner), then
+ * lsw_solve_series with *sp.  Up to max_concurrent problems (<= 0: 4; at
+ * most 7) are worked on at once from host worker threads, each on its own
+ * stream, so that their builds and solves overlap on the GPU.  The call
+ * first synchronises `stream` (inputs may come from it) and returns when
+ * every problem is done.  info: HOST array with one record per source, in
+ * problem order.  Returns LSW_OK, or the first failing problem's status. */
+lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hparams* hp,
+                             const lsw_solve_params* sp, int max_concurrent,
+                             lsw_solve_info* info, void* stream);
+
+/* Measure the operator's pass variants for this grid and precision on
+ * nbatch fields -- 0: register radix-8 FFT passes, 1: the same with
+ * 512-thread row blocks in the x pass, 2: shared-memory Stockham passes --
+ * and use the fastest for this (2nz, 2nx, precision) from now on in this
+ * process.  *variant (may be NULL) receives the choice, ms3 (may be NULL)
+ * the three mean times per apply in ms (-1: variant not available here).
+ * Synchronises the stream. */
+lsw_status lsw_autotune(const lsw_green* g, int prec, int nbatch, void* stream,
+                        int* variant, float* ms3);
+
 #ifdef __cplusplus
 }
 #endif

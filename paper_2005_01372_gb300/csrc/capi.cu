@@ -67,10 +67,13 @@ KTimer::~KTimer() {
 }
 
 namespace {
-constexpr int kPool = 8;
+constexpr int kPool = 8, kSlots = 8;
 std::mutex g_pool_mu;
-cudaStream_t g_pool[64][kPool] = {};
+cudaStream_t g_pool[64][kSlots][kPool] = {};
+thread_local int g_slot = 0;     // which pool this host thread forks onto
 }  // namespace
+
+void set_worker_slot(int slot) { g_slot = slot >= 0 && slot < kSlots ? slot : 0; }
 
 Fork::Fork(cudaStream_t parent) : parent_(parent) {
     int dev = 0;
@@ -78,8 +81,9 @@ Fork::Fork(cudaStream_t parent) : parent_(parent) {
     {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         for (int i = 0; i < kPool; ++i) {
-            if (dev >= 0 && dev < 64 && !g_pool[dev][i]) cudaStreamCreateWithFlags(&g_pool[dev][i], cudaStreamNonBlocking);
-            streams_[i] = (dev >= 0 && dev < 64) ? g_pool[dev][i] : parent;
+            cudaStream_t* slot = (dev >= 0 && dev < 64) ? &g_pool[dev][g_slot][i] : nullptr;
+            if (slot && !*slot) cudaStreamCreateWithFlags(slot, cudaStreamNonBlocking);
+            streams_[i] = slot ? *slot : parent;
         }
     }
     cudaEventCreateWithFlags(&start_, cudaEventDisableTiming);

@@ -13,7 +13,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "fft.cuh"
 #include "lsw_internal.cuh"
@@ -206,13 +210,13 @@ k_fa(const typename Cx<R>::T* __restrict__ u, DevGeom geo, const typename Cx<R>:
     }
 }
 
-template <typename R, int LOGP>
-__global__ void __launch_bounds__(256)
+template <typename R, int LOGP, int NTB>
+__global__ void __launch_bounds__(NTB)
 k_fb(typename Cx<R>::T* __restrict__ T, int pz, const typename Cx<R>::T* __restrict__ spt,
      const typename Cx<R>::T* __restrict__ tw, int twstep) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    constexpr int px = 1 << LOGP, bx = px >> 1, Tx = px >> 3, lpc = 256 / Tx;
+    constexpr int px = 1 << LOGP, bx = px >> 1, Tx = px >> 3, lpc = NTB / Tx;
     constexpr int TS = bx + 4;                                   // tile row stride: conflict-free transposes
     const int l = threadIdx.x / Tx, t = threadIdx.x - l * Tx;
     C* tile = reinterpret_cast<C*>(sm_raw);                      // lpc rows of bx
@@ -221,7 +225,7 @@ k_fb(typename Cx<R>::T* __restrict__ T, int pz, const typename Cx<R>::T* __restr
     const int kz0 = blockIdx.x * lpc;
     const int nrow = min(lpc, pz - kz0);
     C* Tb = T + (long long)b * pz * bx;
-    for (int e = threadIdx.x; e < lpc * bx; e += 256) {
+    for (int e = threadIdx.x; e < lpc * bx; e += NTB) {
         const int r = e % lpc, ix = e / lpc;
         tile[r * TS + ix] = r < nrow ? Tb[(long long)ix * pz + kz0 + r] : czero<C>();
     }
@@ -248,7 +252,7 @@ k_fb(typename Cx<R>::T* __restrict__ T, int pz, const typename Cx<R>::T* __restr
         if (kx < bx) tile[l * TS + kx] = v[q];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < lpc * bx; e += 256) {
+    for (int e = threadIdx.x; e < lpc * bx; e += NTB) {
         const int r = e % lpc, ix = e / lpc;
         if (r < nrow) Tb[(long long)ix * pz + kz0 + r] = tile[r * TS + ix];
     }
@@ -435,7 +439,7 @@ int grid_for(long long n, int bs = 256) {
 
 // Launch the register-FFT passes for a runtime log2 size (3..11).
 template <typename K>
-lsw_status set_smem(K k, bool& done) {
+lsw_status set_smem(K k, std::atomic<bool>& done) {
     if (!done) {
         LSW_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         done = true;
@@ -460,7 +464,7 @@ lsw_status set_smem(K k, bool& done) {
 template <typename R>
 lsw_status launch_fa(int lg, dim3 grid, size_t sm, cudaStream_t st, const typename Cx<R>::T* u, DevGeom dg,
                      const typename Cx<R>::T* tw, int tws, int adj, typename Cx<R>::T* work) {
-    static bool done[12] = {};
+    static std::atomic<bool> done[12];
     LSW_LOG_SWITCH(lg, {
         LSW_TRY(set_smem(k_fa<R, L_>, done[L_]));
         k_fa<R, L_><<<grid, 256, sm, st>>>(u, dg, tw, tws, adj, work);
@@ -469,13 +473,14 @@ lsw_status launch_fa(int lg, dim3 grid, size_t sm, cudaStream_t st, const typena
     return LSW_OK;
 }
 
-template <typename R>
+template <typename R, int NTB>
 lsw_status launch_fb(int lg, dim3 grid, size_t sm, cudaStream_t st, typename Cx<R>::T* work, int pz,
                      const typename Cx<R>::T* spt, const typename Cx<R>::T* tw, int tws) {
-    static bool done[12] = {};
+    static std::atomic<bool> done[12];
     LSW_LOG_SWITCH(lg, {
-        LSW_TRY(set_smem(k_fb<R, L_>, done[L_]));
-        k_fb<R, L_><<<grid, 256, sm, st>>>(work, pz, spt, tw, tws);
+        if (L_ < 4 && NTB > 256) return LSW_ERR_UNSUPPORTED_SIZE;
+        LSW_TRY(set_smem(k_fb<R, L_, NTB>, done[L_]));
+        k_fb<R, L_, NTB><<<grid, NTB, sm, st>>>(work, pz, spt, tw, tws);
         LSW_LAUNCH_CHECK();
     })
     return LSW_OK;
@@ -485,13 +490,37 @@ template <typename R>
 lsw_status launch_fc(int lg, dim3 grid, size_t sm, cudaStream_t st, const typename Cx<R>::T* work, DevGeom dg,
                      const typename Cx<R>::T* tw, int tws, int mode, const typename Cx<R>::T* u,
                      const typename Cx<R>::T* u0, typename Cx<R>::T* y) {
-    static bool done[12] = {};
+    static std::atomic<bool> done[12];
     LSW_LOG_SWITCH(lg, {
         LSW_TRY(set_smem(k_fc<R, L_>, done[L_]));
         k_fc<R, L_><<<grid, 256, sm, st>>>(work, dg, tw, tws, mode, u, u0, y);
         LSW_LAUNCH_CHECK();
     })
     return LSW_OK;
+}
+
+// ---------------------------------------------------------- pass tuning
+// Variant of the operator passes per (2bz, 2bx, precision): 0 register FFT
+// with 256-thread row CTAs in pass B, 1 the same with 512-thread row CTAs,
+// 2 the shared-memory Stockham passes.  Chosen by lsw_autotune.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+thread_local int g_force_variant = -1;
+}  // namespace
+
+int op_variant(int pz, int px, int rsize) {
+    if (g_force_variant >= 0) return g_force_variant;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(pz, px, rsize));
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+void op_force_variant(int v) { g_force_variant = v; }
+
+void op_set_variant(int pz, int px, int rsize, int v) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(pz, px, rsize)] = v;
 }
 
 // ------------------------------------------------------------ op_apply
@@ -511,9 +540,11 @@ lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, i
 
     DevGeom dg{bz, bx, ilog2(bz), geo.chi, geo.chi_ld, geo.origin, geo.vpb > 0 ? geo.vpb : 1};
     const int logpz = ilog2(pz), logpx = ilog2(px);
-    if (pz >= 8 && px >= 8 && pz <= 2048 && px <= 2048 && sp.t32 && sp.t64) {
+    const int variant = op_variant(pz, px, (int)sizeof(R));
+    if (variant != 2 && pz >= 8 && px >= 8 && pz <= 2048 && px <= 2048 && sp.t32 && sp.t64) {
         const C* spt = reinterpret_cast<const C*>(sizeof(R) == 8 ? (const void*)sp.t64 : (const void*)sp.t32);
-        const int lz = 256 / (pz >> 3), lx = 256 / (px >> 3);
+        const int ntb = (variant == 1 && px >= 16) ? 512 : 256;
+        const int lz = 256 / (pz >> 3), lx = ntb / (px >> 3);
         const size_t smA = sizeof(C) * (size_t)lz * (pad8h(pz) + 1);
         const size_t smB = sizeof(C) * ((size_t)lx * (bx + 4) + (size_t)lx * (pad8h(px) + 1));
         const int twz = g->twP / pz, twx = g->twP / px;
@@ -521,7 +552,8 @@ lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, i
         KTimer kt(sizeof(R) == 8 ? "operator_c128" : "operator_c64", st, op_bytes(sizeof(C), bz, bx, nbatch, u0 != nullptr, mode),
                   op_flops(bz, bx, nbatch));
         LSW_TRY(launch_fa<R>(logpz, gA, smA, st, u, dg, tw, twz, mode == LSW_OP_ADJOINT, work));
-        LSW_TRY(launch_fb<R>(logpx, gB, smB, st, work, pz, spt, tw, twx));
+        if (ntb == 512) LSW_TRY((launch_fb<R, 512>(logpx, gB, smB, st, work, pz, spt, tw, twx)));
+        else LSW_TRY((launch_fb<R, 256>(logpx, gB, smB, st, work, pz, spt, tw, twx)));
         LSW_TRY(launch_fc<R>(logpz, gA, smA, st, work, dg, tw, twz, mode, u, u0, y));
         return LSW_OK;
     }
@@ -535,7 +567,7 @@ lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, i
     auto ka = k_pass_a<R, NT, MB4>;
     auto kb = k_pass_b<R, NT, MB4>;
     auto kc = k_pass_c<R, NT, MB4>;
-    static bool attr_done[2] = {false, false};
+    static std::atomic<bool> attr_done[2];
     if (!attr_done[sizeof(R) == 8]) {
         const int maxsm = 200 * 1024;
         LSW_CUDA(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "lsw_internal.cuh"
@@ -1336,7 +1337,7 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
         const int ksplit = (k + kchunk - 1) / kchunk;
         DevBuf part;
         LSW_TRY(part.alloc(sizeof(CT) * (size_t)ksplit * batch * m * n, st));
-        static bool attr_cn[2] = {false, false};
+        static std::atomic<bool> attr_cn[2];
         if (!attr_cn[sizeof(R) == 8]) {
             LSW_CUDA(cudaFuncSetAttribute(k_gemm_cn_small<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
             attr_cn[sizeof(R) == 8] = true;
@@ -1353,7 +1354,7 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
     if (oa == 0 && ob == 0 && k <= 64 && n <= 64) {
         const int ngrp = (n + 15) / 16;
         const int rows_per = 256 / ngrp;
-        static bool attr_nn[2] = {false, false};
+        static std::atomic<bool> attr_nn[2];
         if (!attr_nn[sizeof(R) == 8]) {
             LSW_CUDA(cudaFuncSetAttribute(k_gemm_nn_smallk<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
             attr_nn[sizeof(R) == 8] = true;
@@ -1409,7 +1410,7 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
     constexpr int NT = 512;
     const size_t cap = 200 * 1024;
     int cmax = (int)std::min<size_t>(1024, (cap / sizeof(CT) - (size_t)k * k) / k);
-    static bool attr[2] = {false, false};
+    static std::atomic<bool> attr[2];
     if (!attr[sizeof(R) == 8]) {
         LSW_CUDA(cudaFuncSetAttribute(k_tsqr_chunk<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
         LSW_CUDA(cudaFuncSetAttribute(k_tsqr_apply<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
@@ -1471,7 +1472,7 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
     const size_t per = sizeof(CT) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2) + sizeof(int) * 64;
     const size_t perA = (per + 15) & ~size_t(15);
     const int wpc = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / perA));
-    static bool attr[2] = {false, false};
+    static std::atomic<bool> attr[2];
     if (!attr[sizeof(R) == 8]) {
         LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi_warp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr[sizeof(R) == 8] = true;
@@ -1482,7 +1483,7 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
-    static bool attrb[2] = {false, false};
+    static std::atomic<bool> attrb[2];
     if (!attrb[sizeof(R) == 8]) {
         LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         attrb[sizeof(R) == 8] = true;
@@ -1550,7 +1551,7 @@ lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cuda
     int nb = 16;
     while (nb > 1 && (size_t)n * nb * sizeof(CT) > cap) nb >>= 1;
     if ((size_t)n * nb * sizeof(CT) > cap) return LSW_ERR_UNSUPPORTED_SIZE;
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         LSW_CUDA(cudaFuncSetAttribute(k_gj_panel<CT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
         attr = true;

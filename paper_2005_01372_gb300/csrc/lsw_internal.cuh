@@ -108,6 +108,9 @@ struct DevBuf {
 // Fork independent work from a parent stream onto library-owned streams and
 // join it back: child(i) starts after everything enqueued on the parent so
 // far; join() makes the parent wait for every child used.
+// Host worker threads of a batched call fork onto their own stream pools.
+void set_worker_slot(int slot);
+
 class Fork {
   public:
     explicit Fork(cudaStream_t parent);

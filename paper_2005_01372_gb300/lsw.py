@@ -54,6 +54,11 @@ class _SolveParams(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [("grid", _Grid), ("velocity", ctypes.c_void_p), ("sources", ctypes.POINTER(ctypes.c_int32)),
+                ("nsrc", ctypes.c_int32), ("pad_", ctypes.c_int32), ("u", ctypes.c_void_p)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("pad_", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
@@ -85,6 +90,9 @@ _SIGS = {
     "lsw_apply_precond": (I32, [VP, VP, VP, I32, VP]),
     "lsw_solve_series": (I32, [VP, VP, VP, VP, VP, I32, ctypes.POINTER(_SolveParams),
                                ctypes.POINTER(SolveInfo), VP]),
+    "lsw_solve_batched": (I32, [VP, I32, ctypes.POINTER(_HParams), ctypes.POINTER(_SolveParams), I32,
+                                ctypes.POINTER(SolveInfo), VP]),
+    "lsw_autotune": (I32, [VP, I32, I32, VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
 }
 
 
@@ -333,3 +341,41 @@ def solve_series(G: Green, chi, H, u0, u=None, sp: SolveParams = None, stream=No
     if st not in (0, 5, 6, 7) or (check and st != 0):
         _check(st, "lsw_solve_series")
     return u, list(infos)
+
+
+def autotune(G: Green, prec: int = C64, nbatch: int = 32, stream=None):
+    """lsw_autotune: returns (chosen variant, [ms of variants 0, 1, 2])."""
+    v = ctypes.c_int()
+    ms = (ctypes.c_float * 3)()
+    _check(lib().lsw_autotune(G.handle, prec, nbatch, _stream(stream), ctypes.byref(v), ms), "lsw_autotune")
+    return v.value, list(ms)
+
+
+def solve_batched(problems, hp: HParams = None, sp: SolveParams = None, max_concurrent: int = 4, stream=None):
+    """lsw_solve_batched.  ``problems``: list of dicts with keys nz, nx, h, c0,
+    freq_hz, velocity (CUDA float64 tensor), sources (list of (iz, ix)).
+    Returns (list of output tensors, list of per-source SolveInfo lists)."""
+    sp = sp or SolveParams(prec=MIXED)
+    dt = _cdtype(sp.prec)
+    arr = (_Problem * len(problems))()
+    keep, outs = [], []
+    for i, p in enumerate(problems):
+        src = (ctypes.c_int32 * (2 * len(p["sources"])))(*[int(v) for s_ in p["sources"] for v in s_])
+        keep.append(src)
+        u = torch.empty((len(p["sources"]), p["nz"] * p["nx"]), dtype=dt, device="cuda")
+        outs.append(u)
+        arr[i] = _Problem(_Grid(p["nz"], p["nx"], p["h"], p["c0"], p["freq_hz"]),
+                          _ptr(p["velocity"], torch.float64), src, len(p["sources"]), 0, _ptr(u))
+    total = sum(len(p["sources"]) for p in problems)
+    infos = (SolveInfo * max(1, total))()
+    hpc = hp.c() if hp is not None else None
+    spc = sp.c()
+    st = lib().lsw_solve_batched(arr, len(problems), ctypes.byref(hpc) if hpc is not None else None,
+                                 ctypes.byref(spc), max_concurrent, infos, _stream(stream))
+    if st not in (0, 5, 6, 7):
+        _check(st, "lsw_solve_batched")
+    res, k = [], 0
+    for p in problems:
+        res.append([infos[k + j] for j in range(len(p["sources"]))])
+        k += len(p["sources"])
+    return outs, res
