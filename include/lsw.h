@@ -107,7 +107,8 @@ typedef struct {
     int32_t iterations;   /* series steps taken (inner steps summed for MIXED) */
     int32_t outer;        /* refinement steps (MIXED), else 0                  */
     int32_t status;       /* LSW_OK, LSW_ERR_NOT_CONVERGED, ...                */
-    int32_t pad_;
+    int32_t fallback;     /* lsw_solve_learned: 1 if the learned preconditioner
+                             was dropped for H during the solve, else 0       */
     double rel_residual;  /* final ||psi0 - (I - G0V) psi|| / ||psi0||, FP64   */
 } lsw_solve_info;
 
@@ -276,6 +277,80 @@ lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hpar
  * Synchronises the stream. */
 lsw_status lsw_autotune(const lsw_green* g, int prec, int nbatch, void* stream,
                         int* variant, float* ms3);
+
+/* ------------------------------------------------------------------------
+ * Learned right preconditioner.  The paper has no network: its Sec. 3.2
+ * compares the preconditioned series with GMRES, and this is a Fourier
+ * neural operator that stands in for H inside flexible GMRES, with H kept as
+ * the fallback.  Everything runs in FP32 complex.
+ *
+ * Network.  Input x: two complex channels on the nz x nx grid (strip order),
+ *   x0 = r / ||r||_2 and x1 = chi / k0^2 + i k0 h  (chi / k0^2 = c0^2/c^2 - 1).
+ *   v = P x + p  (P: W x 2);  for l < L:  v <- sigma(K_l v + W_l v + b_l),
+ *   sigma = split GELU gelu(Re) + i gelu(Im), none on the last layer;
+ *   y = Q v + q  (Q: 1 x W).  K_l is a spectral convolution on the 2m x 2m
+ *   modes kz, kx in {0..m-1} U {n-m..n-1} of the unnormalised 2D DFT F:
+ *   K_l v = F^-1 (R_l[k] (F v)[k]) with one W x W complex matrix per mode.
+ * Parameters: one FP32-complex device buffer of lsw_fno_num_params entries,
+ *   column-major blocks in this order: P^T (2 x W), p (W); per layer R_l
+ *   ((2m)^2 modes, mode index a + 2m b for kz-mode a and kx-mode b, each
+ *   W x W with entry (o, i) = R_l[a, b][o][i]), W_l^T (W x W), b_l (W); then
+ *   Q^T (W), q (1).
+ * Gradients: G = dL/dRe + i dL/dIm of L = mean |y - target|^2 over all
+ *   batch * nz * nx outputs, in the same layout.
+ * Adam: Kingma & Ba (2015) on real and imaginary parts separately,
+ *   beta1 0.9, beta2 0.999, eps 1e-8, moments kept in the handle.
+ * ---------------------------------------------------------------------- */
+typedef struct lsw_fno lsw_fno;           /* weights, gradients, Adam moments */
+
+typedef struct {
+    int32_t nz, nx;       /* grid of every input and output field (>= 2)          */
+    int32_t width;        /* W channels, 1..64                                    */
+    int32_t modes;        /* m: 2m retained wavenumbers per axis, 2m <= nz, nx    */
+    int32_t layers;       /* L, 1..16                                             */
+    int32_t pad_;
+    uint64_t seed;        /* Philox4x32-10 key of the Gaussian initial weights    */
+} lsw_fno_params;
+
+/* Create a network with Gaussian weights scaled by 1/sqrt(fan-in) (R_l by
+ * 1/W) and zero biases, initialised by work enqueued on `stream`. */
+lsw_status lsw_fno_create(const lsw_fno_params* p, void* stream, lsw_fno** out);
+lsw_status lsw_fno_destroy(lsw_fno* f);
+/* Number of complex parameters (host). */
+lsw_status lsw_fno_num_params(const lsw_fno* f, int64_t* count);
+/* Copy one state buffer out (dst != NULL) and/or in (src != NULL): which =
+ * 0 weights, 1 gradients, 2 Adam first moments (complex), 3 Adam second
+ * moments (per entry: second moment of the real part, of the imaginary part).
+ * Device buffers of lsw_fno_num_params complex64 entries. */
+lsw_status lsw_fno_state(lsw_fno* f, int which, void* dst, const void* src, void* stream);
+/* y = network(x): x is batch x 2 fields, y batch fields, complex64, device. */
+lsw_status lsw_fno_forward(const lsw_fno* f, const void* x, void* y, int batch, void* stream);
+/* Forward, loss and backward on one batch; the gradients stay in the handle
+ * (grad, device, may be NULL: a copy of them).  loss (HOST, may be NULL)
+ * receives L, which synchronises the stream. */
+lsw_status lsw_fno_loss_grad(lsw_fno* f, const void* x, const void* target, int batch,
+                             double* loss, void* grad, void* stream);
+/* One Adam update with the handle's gradients; t >= 1 is the step number
+ * (bias corrections 1 - beta^t), so a resumed run passes its own count. */
+lsw_status lsw_fno_adam_step(lsw_fno* f, float lr, int32_t t, void* stream);
+/* The preconditioner: z_b = ||v_b|| * network([v_b / ||v_b||, chi/k0^2 + i k0 h])
+ * for nbatch fields v (prec LSW_C128 or LSW_C64, device), on g's grid, which
+ * must match the network's. */
+lsw_status lsw_fno_apply(const lsw_fno* f, const lsw_green* g, const double* chi, const void* v,
+                         void* z, int nbatch, int prec, void* stream);
+
+/* FGMRES (sp->method must be LSW_FGMRES) with the network as right
+ * preconditioner.  The preconditioner is fixed for the whole batch of
+ * sources: when, five iterations into a restart cycle, some active source's
+ * residual estimate has not dropped below 0.9 times its value at the start
+ * of the cycle, the cycle ends and H (NULL: none) takes over for the rest of
+ * the call (the cut-off cycle does not update psi); info[s].fallback reports
+ * it.  Otherwise as lsw_solve_series
+ * (precisions, LSW_MIXED refinement, FP64 final residual); H, when given,
+ * must be stored in the inner precision. */
+lsw_status lsw_solve_learned(const lsw_green* g, const double* chi, const lsw_fno* fno,
+                             const lsw_hmatrix* h, const void* u0, void* u, int nbatch,
+                             const lsw_solve_params* sp, lsw_solve_info* info, void* stream);
 
 #ifdef __cplusplus
 }

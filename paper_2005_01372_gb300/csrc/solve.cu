@@ -19,6 +19,16 @@ namespace lsw {
 template <typename R>
 lsw_status apply_h(const lsw_hmatrix* h, const typename Cx<R>::T* x, typename Cx<R>::T* y, int nb, cudaStream_t st);
 int hmatrix_prec(const lsw_hmatrix* h);
+lsw_status fno_apply_precond(const lsw_fno* f, const lsw_green* g, const double* chi, const void* v, void* z, int nb,
+                             int prec, cudaStream_t st);
+bool fno_matches(const lsw_fno* f, const lsw_green* g);
+
+// The learned right preconditioner of a solve and whether it has been
+// dropped for H.
+struct Learned {
+    const lsw_fno* fno = nullptr;
+    bool off = false;
+};
 
 namespace {
 
@@ -161,12 +171,19 @@ lsw_status series_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
 
 // ----------------------------------------------------------------- FGMRES
 // Flexible GMRES(m) for nb independent sources in lockstep, from x = 0, with
-// H as right preconditioner; Arnoldi by classical Gram-Schmidt applied twice,
-// the small least-squares problems by Givens rotations on the host in FP64.
+// H (or the learned network while it is on) as right preconditioner; Arnoldi
+// by classical Gram-Schmidt applied twice, the small least-squares problems
+// by Givens rotations on the host in FP64.  A cycle preconditioned by the
+// network that has not cut every active source's residual estimate below
+// 0.9 x its start after kProbe iterations ends there, without updating x,
+// and turns the network off for the rest of the solve.
+constexpr int kProbe = 5;
+constexpr double kProbeRatio = 0.9;
+
 template <typename R>
 lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const typename Cx<R>::T* b,
                       typename Cx<R>::T* x, int nb, int m, int max_iter, double tol, std::vector<SrcInfo>& info,
-                      cudaStream_t st) {
+                      cudaStream_t st, Learned* lp = nullptr) {
     typedef typename Cx<R>::T C;
     typedef std::complex<double> Z;
     const long long n = (long long)g->nz * g->nx;
@@ -191,7 +208,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     std::vector<Z> H((size_t)nb * (m + 1) * m), gv((size_t)nb * (m + 1)), cs((size_t)nb * m), sn((size_t)nb * m);
     std::vector<C> hh((size_t)(m + 1) * nb), yh((size_t)m * nb);
     std::vector<int> kused(nb, 0), conv(nb, 0), its(nb, 0);
-    std::vector<double> scale(nb);
+    std::vector<double> scale(nb), beta0(nb);
     const C one_ = mk((R)1, (R)0), zero_ = mk((R)0, (R)0), mone = mk((R)-1, (R)0);
     int total = 0;
     const size_t pitchV = sizeof(C) * n * (m + 1), pitchZ = sizeof(C) * n * m, row = sizeof(C) * n;
@@ -213,6 +230,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
         if (!left) break;
         for (int s = 0; s < nb; ++s) {
             const double beta = std::sqrt(nr[s]);
+            beta0[s] = beta;
             scale[s] = (!done[s] && beta > 0) ? -1.0 / beta : 0.0;
             for (int i = 0; i <= m; ++i) gv[(size_t)s * (m + 1) + i] = 0;
             gv[(size_t)s * (m + 1)] = done[s] ? 0.0 : beta;
@@ -223,10 +241,14 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
         k_scale_cast<C, C><<<gridn(n * nb), 256, 0, st>>>(w.as<C>(), vj.as<C>(), ysc.as<double>(), n, nb);
         LSW_LAUNCH_CHECK();
         LSW_CUDA(cudaMemcpy2DAsync(V.p, pitchV, vj.p, row, row, nb, cudaMemcpyDeviceToDevice, st));
+        const bool learned = lp && lp->fno && !lp->off;
+        bool stalled = false;
         int j = 0;
         for (; j < m; ++j) {
-            // z_j = H v_j ; w = A z_j
-            if (h) LSW_TRY(apply_h<R>(h, vj.as<C>(), zj.as<C>(), nb, st));
+            // z_j = H v_j (or the network's z_j) ; w = A z_j
+            if (learned)
+                LSW_TRY(fno_apply_precond(lp->fno, g, chi, vj.p, zj.p, nb, sizeof(R) == 8 ? LSW_C128 : LSW_C64, st));
+            else if (h) LSW_TRY(apply_h<R>(h, vj.as<C>(), zj.as<C>(), nb, st));
             else LSW_CUDA(cudaMemcpyAsync(zj.p, vj.p, sizeof(C) * n * nb, cudaMemcpyDeviceToDevice, st));
             LSW_CUDA(cudaMemcpy2DAsync(Zb.as<char>() + row * j, pitchZ, zj.p, row, row, nb, cudaMemcpyDeviceToDevice, st));
             LSW_TRY(op_full<R>(g, chi, LSW_OP_RESIDUAL, zj.as<C>(), nullptr, w.as<C>(), nb, work, st));
@@ -283,9 +305,14 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
                 const double est = std::abs(gs[j + 1]) / std::sqrt(nrmb[s]);
                 if (est <= tol || nr[s] == 0) conv[s] = 1;
                 else ++still;
+                if (learned && j + 1 == kProbe && std::abs(gs[j + 1]) > kProbeRatio * beta0[s]) stalled = true;
             }
-            if (!still || total >= max_iter) { ++j; break; }
+            if (stalled) lp->off = true;
+            if (!still || total >= max_iter || stalled) { ++j; break; }
         }
+        // a stalled cycle's directions came from a network that does not
+        // help here: its update is dropped and the next cycle restarts from x
+        if (stalled) continue;
         // x += Z y  with R y = g (back substitution per source)
         for (int s = 0; s < nb; ++s) {
             for (int i = 0; i < m; ++i) yh[(size_t)s * m + i] = mk((R)0, (R)0);
@@ -313,8 +340,8 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
 template <typename R>
 lsw_status inner_run(int method, const lsw_green* g, const double* chi, const lsw_hmatrix* h,
                      const typename Cx<R>::T* b, typename Cx<R>::T* x, int nb, const lsw_solve_params* sp, double tol,
-                     std::vector<SrcInfo>& info, cudaStream_t st) {
-    if (method == LSW_FGMRES) return fgmres_run<R>(g, chi, h, b, x, nb, sp->restart, sp->max_iter, tol, info, st);
+                     std::vector<SrcInfo>& info, cudaStream_t st, Learned* lp) {
+    if (method == LSW_FGMRES) return fgmres_run<R>(g, chi, h, b, x, nb, sp->restart, sp->max_iter, tol, info, st, lp);
     return series_run<R>(g, chi, h, b, x, nb, sp->max_iter, tol, info, st);
 }
 
@@ -351,7 +378,7 @@ lsw_status fp64_residual(const lsw_green* g, const double* chi, const typename C
 // Mixed precision: FP64 residual outside, FP32 corrections inside.
 lsw_status mixed_run(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const double2* u0, double2* u,
                      int nb, const lsw_solve_params* sp, std::vector<SrcInfo>& info, std::vector<int>& outer,
-                     cudaStream_t st) {
+                     cudaStream_t st, Learned* lp) {
     const long long n = (long long)g->nz * g->nx;
     DevBuf a, r32, d32, work, dn, act, sc;
     LSW_TRY(a.alloc(sizeof(double2) * n * nb, st));
@@ -387,7 +414,7 @@ lsw_status mixed_run(const lsw_green* g, const double* chi, const lsw_hmatrix* h
         LSW_LAUNCH_CHECK();
         std::vector<SrcInfo> in;
         LSW_TRY(inner_run<float>(sp->method, g, chi, h, r32.as<float2>(), d32.as<float2>(), nb, sp, sp->inner_tol, in,
-                                 st));
+                                 st, lp));
         for (int s = 0; s < nb; ++s)
             if (active[s]) info[s].iters += in[s].iters;
         LSW_TRY(up(act, active, st));
@@ -400,19 +427,19 @@ lsw_status mixed_run(const lsw_green* g, const double* chi, const lsw_hmatrix* h
 }  // namespace
 
 lsw_status solve(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const void* u0, void* u, int nb,
-                 const lsw_solve_params* sp, lsw_solve_info* out, cudaStream_t st) {
+                 const lsw_solve_params* sp, lsw_solve_info* out, cudaStream_t st, Learned* lp) {
     std::vector<SrcInfo> info;
     std::vector<int> outer(nb, 0);
     std::vector<double> rel;
     const int method = sp->method;
     if (sp->prec == LSW_MIXED) {
-        LSW_TRY(mixed_run(g, chi, h, (const double2*)u0, (double2*)u, nb, sp, info, outer, st));
+        LSW_TRY(mixed_run(g, chi, h, (const double2*)u0, (double2*)u, nb, sp, info, outer, st, lp));
         for (int s = 0; s < nb; ++s) rel.push_back(info[s].rel);
     } else if (sp->prec == LSW_C128) {
-        LSW_TRY(inner_run<double>(method, g, chi, h, (const double2*)u0, (double2*)u, nb, sp, sp->tol, info, st));
+        LSW_TRY(inner_run<double>(method, g, chi, h, (const double2*)u0, (double2*)u, nb, sp, sp->tol, info, st, lp));
         LSW_TRY(fp64_residual<double>(g, chi, (const double2*)u, (const double2*)u0, nb, rel, st));
     } else {
-        LSW_TRY(inner_run<float>(method, g, chi, h, (const float2*)u0, (float2*)u, nb, sp, sp->tol, info, st));
+        LSW_TRY(inner_run<float>(method, g, chi, h, (const float2*)u0, (float2*)u, nb, sp, sp->tol, info, st, lp));
         LSW_TRY(fp64_residual<float>(g, chi, (const float2*)u, (const float2*)u0, nb, rel, st));
     }
     lsw_status first = LSW_OK;
@@ -420,6 +447,7 @@ lsw_status solve(const lsw_green* g, const double* chi, const lsw_hmatrix* h, co
         out[s].iterations = info[s].iters;
         out[s].outer = outer[s];
         out[s].status = info[s].status;
+        out[s].fallback = lp && lp->off ? 1 : 0;
         out[s].rel_residual = rel[s];
         if (first == LSW_OK && info[s].status != LSW_OK) first = info[s].status;
     }
@@ -430,9 +458,9 @@ lsw_status solve(const lsw_green* g, const double* chi, const lsw_hmatrix* h, co
 
 using namespace lsw;
 
-extern "C" lsw_status lsw_solve_series(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const void* u0,
-                                       void* u, int nbatch, const lsw_solve_params* sp, lsw_solve_info* info,
-                                       void* stream) {
+namespace {
+lsw_status check_solve(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const void* u0, void* u,
+                       int nbatch, const lsw_solve_params* sp, lsw_solve_info* info) {
     if (!g || !chi || !sp || !info || nbatch < 0) return LSW_ERR_INVALID_ARG;
     if (nbatch == 0) return LSW_OK;
     if (!u0 || !u || u0 == u) return LSW_ERR_INVALID_ARG;
@@ -445,5 +473,27 @@ extern "C" lsw_status lsw_solve_series(const lsw_green* g, const double* chi, co
         const int want = sp->prec == LSW_C128 ? LSW_C128 : LSW_C64;
         if (hp != want) return LSW_ERR_INVALID_ARG;
     }
-    return solve(g, chi, h, u0, u, nbatch, sp, info, reinterpret_cast<cudaStream_t>(stream));
+    return LSW_OK;
+}
+}  // namespace
+
+extern "C" lsw_status lsw_solve_series(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const void* u0,
+                                       void* u, int nbatch, const lsw_solve_params* sp, lsw_solve_info* info,
+                                       void* stream) {
+    LSW_TRY(check_solve(g, chi, h, u0, u, nbatch, sp, info));
+    if (nbatch == 0) return LSW_OK;
+    return solve(g, chi, h, u0, u, nbatch, sp, info, reinterpret_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" lsw_status lsw_solve_learned(const lsw_green* g, const double* chi, const lsw_fno* fno,
+                                        const lsw_hmatrix* h, const void* u0, void* u, int nbatch,
+                                        const lsw_solve_params* sp, lsw_solve_info* info, void* stream) {
+    if (!fno) return LSW_ERR_INVALID_ARG;
+    LSW_TRY(check_solve(g, chi, h, u0, u, nbatch, sp, info));
+    if (sp->method != LSW_FGMRES) return LSW_ERR_INVALID_ARG;
+    if (nbatch == 0) return LSW_OK;
+    if (!fno_matches(fno, g)) return LSW_ERR_INVALID_ARG;
+    Learned lp;
+    lp.fno = fno;
+    return solve(g, chi, h, u0, u, nbatch, sp, info, reinterpret_cast<cudaStream_t>(stream), &lp);
 }

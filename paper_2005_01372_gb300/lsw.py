@@ -61,7 +61,13 @@ class _Problem(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+                ("fallback", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+
+class _FnoParams(ctypes.Structure):
+    _fields_ = [("nz", ctypes.c_int32), ("nx", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("modes", ctypes.c_int32), ("layers", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -93,6 +99,16 @@ _SIGS = {
     "lsw_solve_batched": (I32, [VP, I32, ctypes.POINTER(_HParams), ctypes.POINTER(_SolveParams), I32,
                                 ctypes.POINTER(SolveInfo), VP]),
     "lsw_autotune": (I32, [VP, I32, I32, VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "lsw_fno_create": (I32, [ctypes.POINTER(_FnoParams), VP, ctypes.POINTER(VP)]),
+    "lsw_fno_destroy": (I32, [VP]),
+    "lsw_fno_num_params": (I32, [VP, ctypes.POINTER(ctypes.c_int64)]),
+    "lsw_fno_state": (I32, [VP, I32, VP, VP, VP]),
+    "lsw_fno_forward": (I32, [VP, VP, VP, I32, VP]),
+    "lsw_fno_loss_grad": (I32, [VP, VP, VP, I32, ctypes.POINTER(ctypes.c_double), VP, VP]),
+    "lsw_fno_adam_step": (I32, [VP, ctypes.c_float, ctypes.c_int32, VP]),
+    "lsw_fno_apply": (I32, [VP, VP, VP, VP, VP, I32, I32, VP]),
+    "lsw_solve_learned": (I32, [VP, VP, VP, VP, VP, VP, I32, ctypes.POINTER(_SolveParams),
+                                ctypes.POINTER(SolveInfo), VP]),
 }
 
 
@@ -379,3 +395,90 @@ def solve_batched(problems, hp: HParams = None, sp: SolveParams = None, max_conc
         res.append([infos[k + j] for j in range(len(p["sources"]))])
         k += len(p["sources"])
     return outs, res
+
+
+FNO_WEIGHTS, FNO_GRADS, FNO_ADAM_M, FNO_ADAM_V = 0, 1, 2, 3
+
+
+class FNO:
+    """lsw_fno handle: the learned right preconditioner (weights, gradients
+    and Adam moments on the device, FP32 complex)."""
+
+    def __init__(self, nz: int, nx: int, width: int = 16, modes: int = 8, layers: int = 4, seed: int = 0,
+                 stream=None):
+        self.nz, self.nx, self.width, self.modes, self.layers = nz, nx, width, modes, layers
+        self.n = nz * nx
+        p = _FnoParams(nz, nx, width, modes, layers, 0, seed)
+        out = VP()
+        _check(lib().lsw_fno_create(ctypes.byref(p), _stream(stream), ctypes.byref(out)), "lsw_fno_create")
+        self._h = out
+        c = ctypes.c_int64()
+        _check(lib().lsw_fno_num_params(self._h, ctypes.byref(c)), "lsw_fno_num_params")
+        self.num_params = c.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lsw_fno_destroy(self._h)
+            self._h = None
+
+    def get(self, which: int = FNO_WEIGHTS, stream=None) -> torch.Tensor:
+        t = torch.empty(self.num_params, dtype=torch.complex64, device="cuda")
+        _check(lib().lsw_fno_state(self._h, which, _ptr(t), None, _stream(stream)), "lsw_fno_state")
+        return t
+
+    def set(self, t: torch.Tensor, which: int = FNO_WEIGHTS, stream=None):
+        if t.numel() != self.num_params:
+            raise ValueError("wrong number of parameters")
+        _check(lib().lsw_fno_state(self._h, which, None, _ptr(t, torch.complex64), _stream(stream)),
+               "lsw_fno_state")
+
+    def forward(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        """x: (batch, 2, n) complex64 -> (batch, n)."""
+        b = x.numel() // (2 * self.n)
+        y = torch.empty((b, self.n), dtype=torch.complex64, device="cuda")
+        _check(lib().lsw_fno_forward(self._h, _ptr(x, torch.complex64), _ptr(y), b, _stream(stream)),
+               "lsw_fno_forward")
+        return y
+
+    def loss_grad(self, x: torch.Tensor, target: torch.Tensor, want_grad: bool = False, stream=None):
+        """Mean squared error and its gradient (kept in the handle; a copy
+        is returned with want_grad)."""
+        b = x.numel() // (2 * self.n)
+        g = torch.empty(self.num_params, dtype=torch.complex64, device="cuda") if want_grad else None
+        loss = ctypes.c_double()
+        _check(lib().lsw_fno_loss_grad(self._h, _ptr(x, torch.complex64), _ptr(target, torch.complex64), b,
+                                       ctypes.byref(loss), _ptr(g) if g is not None else None, _stream(stream)),
+               "lsw_fno_loss_grad")
+        return (loss.value, g) if want_grad else loss.value
+
+    def adam_step(self, lr: float, t: int, stream=None):
+        _check(lib().lsw_fno_adam_step(self._h, lr, t, _stream(stream)), "lsw_fno_adam_step")
+
+    def apply(self, G: Green, chi, v: torch.Tensor, z=None, stream=None) -> torch.Tensor:
+        prec = C128 if v.dtype == torch.complex128 else C64
+        nb = v.numel() // self.n
+        if z is None:
+            z = torch.empty_like(v)
+        _check(lib().lsw_fno_apply(self._h, G.handle, _ptr(chi, torch.float64), _ptr(v, v.dtype), _ptr(z, v.dtype),
+                                   nb, prec, _stream(stream)), "lsw_fno_apply")
+        return z
+
+
+def solve_learned(G: Green, chi, fno: FNO, H, u0, u=None, sp: SolveParams = None, stream=None, check: bool = False):
+    """lsw_solve_learned: FGMRES with the network as right preconditioner
+    and H (may be None) as its fallback.  Returns (u, list of SolveInfo)."""
+    sp = sp or SolveParams(prec=C128 if u0.dtype == torch.complex128 else C64, method=FGMRES)
+    nb = u0.numel() // G.n
+    if u is None:
+        u = torch.empty_like(u0)
+    infos = (SolveInfo * nb)()
+    c = sp.c()
+    st = lib().lsw_solve_learned(G.handle, _ptr(chi, torch.float64), fno.handle, H.handle if H is not None else None,
+                                 _ptr(u0, u0.dtype), _ptr(u, u0.dtype), nb, ctypes.byref(c), infos, _stream(stream))
+    if st not in (0, 5, 6, 7) or (check and st != 0):
+        _check(st, "lsw_solve_learned")
+    return u, list(infos)

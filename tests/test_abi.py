@@ -55,6 +55,8 @@ def test_binding_struct_sizes_match_header():
     assert ctypes.sizeof(lsw._HParams) == 40
     assert ctypes.sizeof(lsw._SolveParams) == 40
     assert ctypes.sizeof(lsw.SolveInfo) == 24
+    # lsw_fno_params: 6 int32 + uint64
+    assert ctypes.sizeof(lsw._FnoParams) == 32
 
 
 def test_invalid_arguments_fail_without_touching_the_gpu(libpath):

@@ -1,0 +1,237 @@
+"""Parity of the CUDA Fourier neural operator (forward, gradients, Adam, the
+preconditioner apply) with the FP64 oracle, and the learned FGMRES with its
+fallback to H.
+
+The network runs in FP32 complex; its outputs and gradients are held to a
+relative 2-norm error of 1e-4 per tensor (sums of up to n = 512 products per
+DFT entry and per weight gradient, each rounded at 2^-24).  Adam is compared
+from identical gradients, so only its own FP32 arithmetic differs (1e-5)."""
+import numpy as np
+import pytest
+
+from oracle import fno as ofno
+from oracle import operator as oop
+from oracle import solve
+from paper_2005_01372_gb300 import media
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lsw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_01372_gb300 import lsw as L
+    L.lib()
+    return L
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def flat_params(p, L):
+    """The oracle's parameter dict in the library's flat layout."""
+    parts = [p["P"].ravel(), p["p"]]
+    for l in range(L):
+        parts.append(p[f"R{l}"].transpose(1, 0, 3, 2).ravel())   # mode a + 2m b, then (o, i) column-major
+        parts.append(p[f"W{l}"].ravel())                         # W^T column-major
+        parts.append(p[f"b{l}"])
+    parts += [p["Q"][0], p["q"]]
+    return np.concatenate(parts)
+
+
+def to_flat(f):
+    """(nz, nx) field -> strip order ix * nz + iz."""
+    return np.asarray(f).ravel(order="F")
+
+
+def from_flat(v, nz, nx):
+    return np.asarray(v).reshape(nx, nz).T
+
+
+SHAPES = [(16, 32, 4, 3, 3, 3), (32, 16, 8, 4, 2, 2), (16, 16, 3, 2, 1, 1)]   # nz, nx, W, m, L, batch
+
+
+def _net(lsw, nz, nx, W, m, L, seed):
+    params = ofno.init_params(W, m, L, seed)
+    for k in params:        # nonzero biases so that their paths are exercised
+        if k in ("p", "q") or k.startswith("b"):
+            rng = np.random.default_rng(seed + len(k))
+            params[k] = 0.1 * (rng.standard_normal(params[k].shape) + 1j * rng.standard_normal(params[k].shape))
+    net = lsw.FNO(nz, nx, W, m, L, seed=5)
+    flat = flat_params(params, L)
+    assert flat.size == net.num_params
+    net.set(torch.from_numpy(flat.astype(np.complex64)).cuda())
+    return params, net
+
+
+def _inputs(nz, nx, B, seed):
+    rng = np.random.default_rng(seed)
+    xs = [media.complex_field(rng, (2, nz, nx)) for _ in range(B)]
+    ts = [media.complex_field(rng, (nz, nx)) for _ in range(B)]
+    xg = np.stack([np.stack([to_flat(x[0]), to_flat(x[1])]) for x in xs]).astype(np.complex64)
+    tg = np.stack([to_flat(t) for t in ts]).astype(np.complex64)
+    return xs, ts, torch.from_numpy(xg).cuda(), torch.from_numpy(tg).cuda()
+
+
+def _unflat_grads(g, params, L):
+    """Split a flat gradient into the oracle's dict layout."""
+    out, o = {}, 0
+
+    def take(cnt):
+        nonlocal o
+        v = g[o:o + cnt]
+        o += cnt
+        return v
+
+    W = params["p"].size
+    out["P"] = take(2 * W).reshape(W, 2)
+    out["p"] = take(W)
+    for l in range(L):
+        R = params[f"R{l}"]
+        M = R.shape[0]
+        out[f"R{l}"] = take(R.size).reshape(M, M, W, W).transpose(1, 0, 3, 2)
+        out[f"W{l}"] = take(W * W).reshape(W, W)
+        out[f"b{l}"] = take(W)
+    out["Q"] = take(W)[None, :]
+    out["q"] = take(1)
+    assert o == g.size
+    return out
+
+
+@pytest.mark.parametrize("nz,nx,W,m,L,B", SHAPES)
+def test_forward_parity(lsw, nz, nx, W, m, L, B):
+    params, net = _net(lsw, nz, nx, W, m, L, seed=nz + W)
+    xs, _, xg, _ = _inputs(nz, nx, B, seed=7)
+    y = net.forward(xg).cpu().numpy()
+    for b in range(B):
+        ref = ofno.forward(params, xs[b].astype(np.complex64).astype(np.complex128), nz, nx, m)
+        assert _rel(from_flat(y[b], nz, nx), ref) < 1e-4
+
+
+@pytest.mark.parametrize("nz,nx,W,m,L,B", SHAPES)
+def test_loss_and_gradient_parity(lsw, nz, nx, W, m, L, B):
+    params, net = _net(lsw, nz, nx, W, m, L, seed=3 * nz + W)
+    xs, ts, xg, tg = _inputs(nz, nx, B, seed=11)
+    loss, g = net.loss_grad(xg, tg, want_grad=True)
+    ref_loss, ref_g = 0.0, None
+    for b in range(B):
+        x64 = xs[b].astype(np.complex64).astype(np.complex128)
+        t64 = ts[b].astype(np.complex64).astype(np.complex128)
+        lb, gb = ofno.loss_and_grad(params, x64, t64, nz, nx, m)
+        ref_loss += lb / B
+        ref_g = {k: v / B for k, v in gb.items()} if ref_g is None else {k: ref_g[k] + v / B for k, v in gb.items()}
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    gd = _unflat_grads(g.cpu().numpy().astype(np.complex128), params, L)
+    for k in ref_g:
+        assert _rel(gd[k], ref_g[k]) < 1e-4, k
+    # the handle keeps the same gradient
+    assert torch.equal(net.get(lsw.FNO_GRADS), g)
+
+
+def test_adam_parity(lsw):
+    nz, nx, W, m, L = 16, 16, 4, 2, 2
+    params, net = _net(lsw, nz, nx, W, m, L, seed=1)
+    rng = np.random.default_rng(4)
+    state = {}
+    cur = {k: v.astype(np.complex64).astype(np.complex128) for k, v in params.items()}
+    for t in (1, 2, 3):
+        g = media.complex_field(rng, net.num_params).astype(np.complex64)
+        g[::7] *= 1e-3                          # a spread of magnitudes
+        net.set(torch.from_numpy(g).cuda(), lsw.FNO_GRADS)
+        net.adam_step(1e-2, t)
+        ofno.adam_step(cur, _unflat_grads(g.astype(np.complex128), cur, L), state, 1e-2)
+    w = _unflat_grads(net.get().cpu().numpy().astype(np.complex128), cur, L)
+    for k in cur:
+        assert _rel(w[k], cur[k]) < 1e-5, k
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_preconditioner_apply_parity(lsw, dtype):
+    nz, nx, W, m, L = 32, 32, 4, 3, 2
+    params, net = _net(lsw, nz, nx, W, m, L, seed=9)
+    rng = np.random.default_rng(5)
+    c = media.random_field(rng, nz, nx)
+    P = oop.Problem(nz, nx, 10.0, media.C0, 12.0, c)
+    G = lsw.build_green(nz, nx, 10.0, media.C0, 12.0)
+    chi = torch.from_numpy(P.chi.copy()).cuda()
+    v = media.complex_field(rng, (3, nz * nx)) * np.array([[1.0], [1e-3], [40.0]])
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    z = net.apply(G, chi, torch.from_numpy(v).to(tdt).cuda()).cpu().numpy()
+    for b in range(3):
+        x = ofno.input_channels(v[b], P.chi / P.k ** 2, P.k * P.h, nz, nx)
+        ref = np.linalg.norm(v[b]) * ofno.forward(params, x, nz, nx, m)
+        assert _rel(from_flat(z[b], nz, nx), ref) < 1e-4
+
+
+def _identity_net(lsw, nz, nx):
+    """W = 2, one layer: y = x0, so the preconditioner is the identity."""
+    p = {"P": np.array([[1, 0], [0, 0]], complex), "p": np.zeros(2, complex),
+         "R0": np.zeros((2, 2, 2, 2), complex), "W0": np.eye(2, dtype=complex), "b0": np.zeros(2, complex),
+         "Q": np.array([[1, 0]], complex), "q": np.zeros(1, complex)}
+    net = lsw.FNO(nz, nx, 2, 1, 1)
+    net.set(torch.from_numpy(flat_params(p, 1).astype(np.complex64)).cuda())
+    return net
+
+
+def test_learned_identity_matches_plain_fgmres(lsw):
+    nz = nx = 32
+    rng = np.random.default_rng(21)
+    c = media.random_field(rng, nz, nx, lo=1800, hi=2400)
+    G = lsw.build_green(nz, nx, 10.0, media.C0, 10.0)
+    P = oop.Problem(nz, nx, 10.0, media.C0, 10.0, c)
+    chi = torch.from_numpy(P.chi.copy()).cuda()
+    net = _identity_net(lsw, nz, nx)
+    pos = [(0, 4), (17, 20)]
+    u0 = G.point_sources(pos, lsw.C128)
+    sp = lsw.SolveParams(prec=lsw.C128, method=lsw.FGMRES, tol=1e-8, restart=20, max_iter=200)
+    u1, i1 = lsw.solve_series(G, chi, None, u0, sp=sp)
+    u2, i2 = lsw.solve_learned(G, chi, net, None, u0, sp=sp)
+    assert all(i.status == 0 and i.fallback == 0 for i in i2), [(i.status, i.fallback) for i in i2]
+    for a, b in zip(i1, i2):
+        assert abs(a.iterations - b.iterations) <= 1
+    lu = solve.direct(P, P.sources(pos)).T
+    assert _rel(u2.cpu().numpy(), lu) < 1e-7
+
+
+@pytest.mark.parametrize("prec", ["c128", "mixed"])
+def test_blind_network_falls_back_to_h(lsw, prec):
+    """A network that ignores its residual input gives a one-dimensional
+    Krylov space: the probe sees the stall, H takes over, the solve is still
+    certified by the oracle's FP64 residual."""
+    wl = media.gaussian_inclusion_64()
+    P = oop.Problem(64, 64, 10.0, media.C0, wl.freq_hz, wl.velocity)
+    G = lsw.build_green(64, 64, 10.0, media.C0, wl.freq_hz)
+    chi = torch.from_numpy(P.chi.copy()).cuda()
+    params = ofno.init_params(8, 4, 2, 3)
+    params["P"][:, 0] = 0
+    net = lsw.FNO(64, 64, 8, 4, 2)
+    net.set(torch.from_numpy(flat_params(params, 2).astype(np.complex64)).cuda())
+    hprec = lsw.C128 if prec == "c128" else lsw.C64
+    H = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=hprec, levels=2, rank=20, oversample=10,
+                                              seed=1001))
+    pos = [(5, 32), (40, 60)]
+    u0 = G.point_sources(pos, lsw.C128)
+    sp = lsw.SolveParams(prec=lsw.C128 if prec == "c128" else lsw.MIXED, method=lsw.FGMRES, tol=1e-9,
+                         inner_tol=1e-4, restart=30, max_iter=120)
+    u, infos = lsw.solve_learned(G, chi, net, H, u0, sp=sp)
+    assert all(i.status == 0 and i.fallback == 1 for i in infos), [(i.status, i.fallback) for i in infos]
+    res = P.rel_residual(u.cpu().numpy().T, P.sources(pos))
+    assert np.all(res < 1e-9)
+
+
+def test_learned_rejects_bad_arguments(lsw):
+    G = lsw.build_green(32, 32, 10.0, media.C0, 10.0)
+    chi = torch.zeros(32 * 32, dtype=torch.float64, device="cuda")
+    net = lsw.FNO(16, 16, 2, 1, 1)
+    u0 = G.point_sources([(0, 0)], lsw.C128)
+    with pytest.raises(lsw.LswError):          # grid mismatch
+        lsw.solve_learned(G, chi, net, None, u0, sp=lsw.SolveParams(prec=lsw.C128, method=lsw.FGMRES))
+    net32 = lsw.FNO(32, 32, 2, 1, 1)
+    with pytest.raises(lsw.LswError):          # the series cannot take a network
+        lsw.solve_learned(G, chi, net32, None, u0, sp=lsw.SolveParams(prec=lsw.C128, method=lsw.SERIES))
+    with pytest.raises(lsw.LswError):          # too many modes for the grid
+        lsw.FNO(8, 8, 2, 5, 1)
