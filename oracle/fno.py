@@ -17,7 +17,10 @@ the one the library implements, in plain NumPy, FP64:
            M = {0..m-1} U {n-m..n-1} of the 2D DFT:  Vhat = F v  on M x M,
            Zhat[k] = R_l[k] Vhat[k] (W x W complex per mode),  K_l v = F^-1 Zhat
   sigma:   split GELU, gelu(Re z) + i gelu(Im z), gelu(t) = t Phi(t)
-  project: y = Q v + q                     (Q: 1 x W, complex)
+  project: y = x0 + Q v + q                (Q: 1 x W, complex; the input's
+           residual channel passes straight through, so the network learns
+           the correction beyond the identity and the zero network is the
+           identity preconditioner)
 
 Gradients use G = dL/dRe + i dL/dIm for every complex quantity; then a
 complex-linear map z = A w backpropagates as G_w = A^H G_z, and the split
@@ -92,7 +95,7 @@ def forward(params: dict, x: np.ndarray, nz: int, nx: int, modes: int, keep: boo
         cache[f"Vh{l}"], cache[f"z{l}"] = vh, z
         v = split_gelu(z) if l < L - 1 else z
         cache[f"v{l + 1}"] = v
-    y = np.einsum("ow,wzx->ozx", params["Q"], v)[0] + params["q"][0]
+    y = x[0] + np.einsum("ow,wzx->ozx", params["Q"], v)[0] + params["q"][0]
     return (y, cache) if keep else y
 
 

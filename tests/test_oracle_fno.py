@@ -65,6 +65,14 @@ def test_gradients_match_central_differences():
                 assert fd == pytest.approx(an, rel=1e-6, abs=1e-9), (name, idx, part)
 
 
+def test_zero_projection_is_the_identity():
+    """With Q = 0 and q = 0 the output is the residual channel itself."""
+    p, x, _ = _problem(5)
+    p["Q"][:] = 0
+    p["q"][:] = 0
+    assert np.array_equal(fno.forward(p, x, NZ, NX, MODES), x[0])
+
+
 def test_input_gradient_chain_through_lift():
     """The lift's input gradient, checked through P's gradient formula."""
     p, x, t = _problem(4)
