@@ -288,7 +288,8 @@ lsw_status lsw_autotune(const lsw_green* g, int prec, int nbatch, void* stream,
  *   x0 = r / ||r||_2 and x1 = chi / k0^2 + i k0 h  (chi / k0^2 = c0^2/c^2 - 1).
  *   v = P x + p  (P: W x 2);  for l < L:  v <- sigma(K_l v + W_l v + b_l),
  *   sigma = split GELU gelu(Re) + i gelu(Im), none on the last layer;
- *   y = Q v + q  (Q: 1 x W).  K_l is a spectral convolution on the 2m x 2m
+ *   y = x0 + Q v + q  (Q: 1 x W; the residual channel passes through, so the
+ *   zero network is the identity).  K_l is a spectral convolution on the 2m x 2m
  *   modes kz, kx in {0..m-1} U {n-m..n-1} of the unnormalised 2D DFT F:
  *   K_l v = F^-1 (R_l[k] (F v)[k]) with one W x W complex matrix per mode.
  * Parameters: one FP32-complex device buffer of lsw_fno_num_params entries,
@@ -340,12 +341,13 @@ lsw_status lsw_fno_apply(const lsw_fno* f, const lsw_green* g, const double* chi
                          void* z, int nbatch, int prec, void* stream);
 
 /* FGMRES (sp->method must be LSW_FGMRES) with the network as right
- * preconditioner.  The preconditioner is fixed for the whole batch of
- * sources: when, five iterations into a restart cycle, some active source's
- * residual estimate has not dropped below 0.9 times its value at the start
- * of the cycle, the cycle ends and H (NULL: none) takes over for the rest of
- * the call (the cut-off cycle does not update psi); info[s].fallback reports
- * it.  Otherwise as lsw_solve_series
+ * preconditioner.  The preconditioner is the same for the whole batch of
+ * sources.  Its progress is probed every five iterations of a cycle: when
+ * some active source's residual estimate has not dropped below 0.5 times its
+ * value five iterations earlier, the cycle ends and H (NULL: none) takes over
+ * for the rest of the call; a cycle cut off at its first probe does not
+ * update psi, a later one does.  info[s].fallback reports the switch.
+ * Otherwise as lsw_solve_series
  * (precisions, LSW_MIXED refinement, FP64 final residual); H, when given,
  * must be stored in the inner precision. */
 lsw_status lsw_solve_learned(const lsw_green* g, const double* chi, const lsw_fno* fno,

@@ -3,9 +3,10 @@
 // apply, all in FP32 complex on the library's batched GEMMs.
 //
 // Network (complex): v = P x + p;  v <- sigma(K_l v + W_l v + b_l) for
-// l < L (no sigma on the last layer);  y = Q v + q.  K_l keeps the 2m x 2m
+// l < L (no sigma on the last layer);  y = x0 + Q v + q.  K_l keeps the 2m x 2m
 // modes kz, kx in {0..m-1} U {n-m..n-1} of the 2D DFT and mixes channels per
 // mode with R_l[mode] (W x W).  sigma: GELU on real and imaginary parts.
+// The output adds the input's residual channel x0: y = x0 + Q v + q.
 //
 // Layouts.  A field is nz x nx, strip order; a batch of samples holds W
 // fields per sample, sample after sample, so sample b is the column-major
@@ -309,8 +310,10 @@ static lsw_status fno_forward(const lsw_fno* f, const float2* x, float2* y, int 
         k_bias_act<<<gridn(n * W * B), 256, 0, st>>>(z, P + f->ob[l], tp.v[l + 1], n, W, B, l < f->L - 1);
         LSW_LAUNCH_CHECK();
     }
-    // project: y_b (n x 1) = V_b Q^T + q
-    LSW_TRY(gemm<float>('N', 'N', (int)n, 1, W, c1(), tp.v[f->L], (int)n, W * n, P + f->oQT, W, 0, c0(), y, (int)n, n, B,
+    // project: y_b (n x 1) = x0_b + V_b Q^T + q  (the residual channel passes through)
+    LSW_CUDA(cudaMemcpy2DAsync(y, sizeof(float2) * n, x, sizeof(float2) * 2 * n, sizeof(float2) * n, B,
+                               cudaMemcpyDeviceToDevice, st));
+    LSW_TRY(gemm<float>('N', 'N', (int)n, 1, W, c1(), tp.v[f->L], (int)n, W * n, P + f->oQT, W, 0, c1(), y, (int)n, n, B,
                         st));
     k_bias<<<gridn(n * B), 256, 0, st>>>(y, P + f->oq, n, 1, B);
     LSW_LAUNCH_CHECK();

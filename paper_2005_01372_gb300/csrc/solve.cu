@@ -173,12 +173,15 @@ lsw_status series_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
 // Flexible GMRES(m) for nb independent sources in lockstep, from x = 0, with
 // H (or the learned network while it is on) as right preconditioner; Arnoldi
 // by classical Gram-Schmidt applied twice, the small least-squares problems
-// by Givens rotations on the host in FP64.  A cycle preconditioned by the
-// network that has not cut every active source's residual estimate below
-// 0.9 x its start after kProbe iterations ends there, without updating x,
-// and turns the network off for the rest of the solve.
+// by Givens rotations on the host in FP64.  While the network preconditions,
+// every kProbe iterations of a cycle each active source's residual estimate
+// must have dropped below kProbeRatio times its value kProbe iterations
+// earlier; otherwise the cycle ends there and the network is off for the
+// rest of the solve.  A cycle cut at its first probe does not update x (its
+// directions are what failed); a later one does, with directions whose
+// least-squares pivot is negligible against the largest left out.
 constexpr int kProbe = 5;
-constexpr double kProbeRatio = 0.9;
+constexpr double kProbeRatio = 0.5;
 
 template <typename R>
 lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* h, const typename Cx<R>::T* b,
@@ -208,7 +211,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     std::vector<Z> H((size_t)nb * (m + 1) * m), gv((size_t)nb * (m + 1)), cs((size_t)nb * m), sn((size_t)nb * m);
     std::vector<C> hh((size_t)(m + 1) * nb), yh((size_t)m * nb);
     std::vector<int> kused(nb, 0), conv(nb, 0), its(nb, 0);
-    std::vector<double> scale(nb), beta0(nb);
+    std::vector<double> scale(nb), wstart(nb);
     const C one_ = mk((R)1, (R)0), zero_ = mk((R)0, (R)0), mone = mk((R)-1, (R)0);
     int total = 0;
     const size_t pitchV = sizeof(C) * n * (m + 1), pitchZ = sizeof(C) * n * m, row = sizeof(C) * n;
@@ -230,7 +233,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
         if (!left) break;
         for (int s = 0; s < nb; ++s) {
             const double beta = std::sqrt(nr[s]);
-            beta0[s] = beta;
+            wstart[s] = beta;
             scale[s] = (!done[s] && beta > 0) ? -1.0 / beta : 0.0;
             for (int i = 0; i <= m; ++i) gv[(size_t)s * (m + 1) + i] = 0;
             gv[(size_t)s * (m + 1)] = done[s] ? 0.0 : beta;
@@ -290,7 +293,9 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
                 }
                 const Z a = Hs[(size_t)j * (m + 1) + j], bq = Hs[(size_t)j * (m + 1) + j + 1];
                 const double den = std::sqrt(std::norm(a) + std::norm(bq));
-                Z c_ = 1.0, s_ = 0.0;
+                // a direction that adds nothing (den == 0) leaves the residual
+                // estimate where it was
+                Z c_ = 0.0, s_ = 1.0;
                 if (den > 0) { c_ = a / den; s_ = bq / den; }
                 cS[j] = c_;
                 sS[j] = s_;
@@ -305,14 +310,17 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
                 const double est = std::abs(gs[j + 1]) / std::sqrt(nrmb[s]);
                 if (est <= tol || nr[s] == 0) conv[s] = 1;
                 else ++still;
-                if (learned && j + 1 == kProbe && std::abs(gs[j + 1]) > kProbeRatio * beta0[s]) stalled = true;
+                if (learned && (j + 1) % kProbe == 0) {
+                    if (std::abs(gs[j + 1]) > kProbeRatio * wstart[s]) stalled = true;
+                    wstart[s] = std::abs(gs[j + 1]);
+                }
             }
             if (stalled) lp->off = true;
             if (!still || total >= max_iter || stalled) { ++j; break; }
         }
         // a stalled cycle's directions came from a network that does not
         // help here: its update is dropped and the next cycle restarts from x
-        if (stalled) continue;
+        if (stalled && j <= kProbe) continue;
         // x += Z y  with R y = g (back substitution per source)
         for (int s = 0; s < nb; ++s) {
             for (int i = 0; i < m; ++i) yh[(size_t)s * m + i] = mk((R)0, (R)0);
@@ -321,11 +329,14 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
             const Z* Hs = &H[(size_t)s * (m + 1) * m];
             const Z* gs = &gv[(size_t)s * (m + 1)];
             std::vector<Z> y(k);
+            double dmax = 0;
+            for (int i = 0; i < k; ++i) dmax = std::max(dmax, std::abs(Hs[(size_t)i * (m + 1) + i]));
+            const double dmin = learned ? 1e-6 * dmax : 0.0;
             for (int i = k - 1; i >= 0; --i) {
                 Z acc = gs[i];
                 for (int q = i + 1; q < k; ++q) acc -= Hs[(size_t)q * (m + 1) + i] * y[q];
                 const Z d = Hs[(size_t)i * (m + 1) + i];
-                y[i] = std::abs(d) > 0 ? acc / d : Z(0);
+                y[i] = std::abs(d) > dmin ? acc / d : Z(0);
                 yh[(size_t)s * m + i] = mk((R)y[i].real(), (R)y[i].imag());
             }
         }

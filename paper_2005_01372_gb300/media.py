@@ -186,6 +186,31 @@ def marmousi_1024(freq_hz=30.0, nsrc=16, seed=4, n=1024, h=5.0) -> Workload:
     return Workload(f"marmousi-like-{n}x{n}-{freq_hz:g}Hz-{nsrc}src", n, n, h, C0, freq_hz, c, src)
 
 
+def fno_medium(seed: int, n: int, h: float = 10.0, freq=(10.0, 25.0)):
+    """A training or test medium for the learned preconditioner: 8-20 dipping
+    layers (1500-4500 m/s), a salt ellipse with probability 1/2, 1-3 Gaussian
+    anomalies, and a frequency drawn from U(freq).  Returns (velocity, f)."""
+    rng = np.random.default_rng(seed)
+    c = layered(rng, n, n, h)
+    if rng.uniform() < 0.5:
+        c = salt_ellipse(rng, c, h)
+    c = gaussian_anomalies(rng, c, h, sigma_cells=(n / 32.0, n / 8.0))
+    return c, float(rng.uniform(*freq))
+
+
+def smooth_complex_field(rng: np.random.Generator, count: int, nz: int, nx: int,
+                         sigma_cells=(1.0, 6.0)) -> np.ndarray:
+    """``count`` complex fields (count, nz * nx) in strip order: iid complex
+    normal noise smoothed by a Gaussian of a random width per field."""
+    out = np.empty((count, nz * nx), dtype=np.complex128)
+    for i in range(count):
+        s = rng.uniform(*sigma_cells)
+        re = _smooth(rng.standard_normal((nx, nz)), s)
+        im = _smooth(rng.standard_normal((nx, nz)), s)
+        out[i] = (re + 1j * im).ravel()
+    return out
+
+
 def random_field(rng: np.random.Generator, nz: int, nx: int, lo=1500.0, hi=4500.0,
                  smooth_cells=2.0) -> np.ndarray:
     """Smoothed iid uniform velocities, for small randomized test cases."""

@@ -168,12 +168,11 @@ def test_preconditioner_apply_parity(lsw, dtype):
 
 
 def _identity_net(lsw, nz, nx):
-    """W = 2, one layer: y = x0, so the preconditioner is the identity."""
-    p = {"P": np.array([[1, 0], [0, 0]], complex), "p": np.zeros(2, complex),
-         "R0": np.zeros((2, 2, 2, 2), complex), "W0": np.eye(2, dtype=complex), "b0": np.zeros(2, complex),
-         "Q": np.array([[1, 0]], complex), "q": np.zeros(1, complex)}
-    net = lsw.FNO(nz, nx, 2, 1, 1)
-    net.set(torch.from_numpy(flat_params(p, 1).astype(np.complex64)).cuda())
+    """Zero projection: y = x0, so the preconditioner is the identity."""
+    net = lsw.FNO(nz, nx, 4, 2, 2, seed=3)
+    w = net.get()
+    w[-5:] = 0                  # Q^T (W = 4) and q
+    net.set(w)
     return net
 
 
@@ -199,17 +198,19 @@ def test_learned_identity_matches_plain_fgmres(lsw):
 
 @pytest.mark.parametrize("prec", ["c128", "mixed"])
 def test_blind_network_falls_back_to_h(lsw, prec):
-    """A network that ignores its residual input gives a one-dimensional
-    Krylov space: the probe sees the stall, H takes over, the solve is still
-    certified by the oracle's FP64 residual."""
+    """A network whose output ignores its residual input gives a
+    one-dimensional Krylov space: the probe sees the stall, H takes over, the
+    solve is still certified by the oracle's FP64 residual."""
     wl = media.gaussian_inclusion_64()
     P = oop.Problem(64, 64, 10.0, media.C0, wl.freq_hz, wl.velocity)
     G = lsw.build_green(64, 64, 10.0, media.C0, wl.freq_hz)
     chi = torch.from_numpy(P.chi.copy()).cuda()
-    params = ofno.init_params(8, 4, 2, 3)
-    params["P"][:, 0] = 0
-    net = lsw.FNO(64, 64, 8, 4, 2)
-    net.set(torch.from_numpy(flat_params(params, 2).astype(np.complex64)).cuda())
+    # y = x0 - x0 + 0.3 x1: the output ignores the residual
+    params = {"P": np.eye(2, dtype=complex), "p": np.zeros(2, complex),
+              "R0": np.zeros((2, 2, 2, 2), complex), "W0": np.eye(2, dtype=complex), "b0": np.zeros(2, complex),
+              "Q": np.array([[-1.0, 0.3]], complex), "q": np.zeros(1, complex)}
+    net = lsw.FNO(64, 64, 2, 1, 1)
+    net.set(torch.from_numpy(flat_params(params, 1).astype(np.complex64)).cuda())
     hprec = lsw.C128 if prec == "c128" else lsw.C64
     H = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=hprec, levels=2, rank=20, oversample=10,
                                               seed=1001))
@@ -235,3 +236,41 @@ def test_learned_rejects_bad_arguments(lsw):
         lsw.solve_learned(G, chi, net32, None, u0, sp=lsw.SolveParams(prec=lsw.C128, method=lsw.SERIES))
     with pytest.raises(lsw.LswError):          # too many modes for the grid
         lsw.FNO(8, 8, 2, 5, 1)
+
+
+def test_training_pairs_are_corrections(lsw):
+    """Each pair's target t satisfies (I - G0 V) t = x0 (FP64 oracle
+    operator), to the FP32 rounding of the stored pair."""
+    from paper_2005_01372_gb300 import fno_train as ft
+    hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=1, rank=10, oversample=10, seed=3)
+    pairs = ft.make_pairs(32, [5000, 5001], 9, hp)
+    assert len(pairs) == 18
+    for j, seed in ((0, 5000), (13, 5001)):
+        vel, f = media.fno_medium(seed, 32)
+        P = oop.Problem(32, 32, ft.H_CELL, media.C0, f, vel)
+        x0 = pairs.x[j, 0].cpu().numpy().astype(np.complex128)
+        t = pairs.t[j].cpu().numpy().astype(np.complex128)
+        assert abs(np.linalg.norm(x0) - 1) < 1e-6
+        assert np.linalg.norm(P.A(t) - x0) < 1e-5
+        x1 = pairs.x[j, 1].cpu().numpy()
+        assert np.allclose(x1.real, P.chi / P.k ** 2, rtol=1e-6, atol=1e-6)
+        assert np.allclose(x1.imag, P.k * P.h, rtol=1e-6)
+
+
+def test_training_reduces_loss_and_resumes_exactly(lsw, tmp_path):
+    from paper_2005_01372_gb300 import fno_train as ft
+    hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=1, rank=10, oversample=10, seed=3)
+    pairs = ft.make_pairs(32, [5002, 5003, 5004], 12, hp)
+    a = lsw.FNO(32, 32, 8, 4, 2, seed=11)
+    hist = ft.train(a, pairs, 120, 8, 3e-3, seed=2)
+    assert np.mean(hist[-10:]) < 0.7 * np.mean(hist[:5])
+    # 60 steps in one run == 30 steps, checkpoint, reload, 30 more
+    b = lsw.FNO(32, 32, 8, 4, 2, seed=11)
+    ft.train(b, pairs, 60, 8, 3e-3, seed=5)
+    c = lsw.FNO(32, 32, 8, 4, 2, seed=11)
+    ft.train(c, pairs, 60, 8, 3e-3, seed=5, stop=30)
+    ft.save_checkpoint(c, str(tmp_path / "ck.pt"), 30)
+    d, step = ft.load_checkpoint(str(tmp_path / "ck.pt"))
+    assert step == 30
+    ft.train(d, pairs, 60, 8, 3e-3, seed=5, start=30)
+    assert torch.equal(b.get(), d.get())
