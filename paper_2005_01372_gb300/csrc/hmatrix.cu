@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -424,8 +425,188 @@ lsw_status build_level(const lsw_green* g, const double* chi, const Tree& tr, in
 }
 
 // ------------------------------------------------------- subtree products
+// The off-diagonal part of a subtree product, every level at once.  Level q
+// of node (l, c) has cnt_q blocks of nb_q rows; block j's factors F_j, G_j
+// (nb_q x r, column-major) are consecutive, stride nb_q * r.  For every
+// level and block:
+//     T_j = F_j^H X[rows of block j, or of its sibling j ^ 1 if swapA]
+//     Y[rows of block b] += G_b' T_b'  with b' = b (or b ^ 1 if swapC)
+// (X, Y: m x k, ld m, m = the node's rows).  Three launches: partial T over
+// row chunks of every level, the fixed-order reduction of the partials, and
+// one pass over Y adding every level's G T.
+constexpr int kMaxLev = 16;
+
+template <typename C> struct LrLevels {
+    const C* F[kMaxLev];
+    const C* G[kMaxLev];
+    int nb[kMaxLev];
+    int ch[kMaxLev];                // rows per chunk (divides nb)
+    int chunk0[kMaxLev + 1];        // first chunk of each level
+    long long t0[kMaxLev + 1];      // first T block of each level (units of r*k)
+    int nlev;
+};
+
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int swapA, C* __restrict__ P) {
+    constexpr int TR = 32;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C (*Fs)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw);            // r rows
+    C (*Xs)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw) + r;        // k rows
+    int q = 0;
+    while (q + 1 < lv.nlev && (int)blockIdx.x >= lv.chunk0[q + 1]) ++q;
+    const int chn = blockIdx.x - lv.chunk0[q];
+    const int CH = lv.ch[q], nb = lv.nb[q];
+    const int row0 = chn * CH;
+    const int j = row0 / nb, o = row0 - j * nb;
+    const int src = swapA ? (j ^ 1) : j;
+    const C* Fj = lv.F[q] + (long long)j * nb * r;
+    const C* Xs_g = X + (long long)src * nb + o;
+    const int nout = r * k;
+    C acc[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc[t] = czero<C>();
+    for (int r0 = 0; r0 < CH; r0 += TR) {
+        const int nr = min(TR, CH - r0);
+        for (int e = threadIdx.x; e < TR * r; e += 256) {
+            const int cc = e / TR, rr = e - cc * TR;
+            Fs[cc][rr] = rr < nr ? Fj[(long long)cc * nb + o + r0 + rr] : czero<C>();
+        }
+        for (int e = threadIdx.x; e < TR * k; e += 256) {
+            const int cc = e / TR, rr = e - cc * TR;
+            Xs[cc][rr] = rr < nr ? Xs_g[(long long)cc * m + r0 + rr] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int oi = threadIdx.x + 256 * t;
+            if (oi < nout) {
+                const int i = oi % r, jj = oi / r;
+                C sacc = acc[t];
+#pragma unroll 8
+                for (int rr = 0; rr < TR; ++rr) cfmac(sacc, Fs[i][rr], Xs[jj][rr]);
+                acc[t] = sacc;
+            }
+        }
+        __syncthreads();
+    }
+    C* out = P + (long long)blockIdx.x * nout;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const int oi = threadIdx.x + 256 * t;
+        if (oi < nout) out[oi] = acc[t];
+    }
+}
+
+// T[level q][block j] = sum over the block's chunks of the partials, in order.
+template <typename C>
+__global__ void k_lr_reduce(LrLevels<C> lv, int r, int k, const C* __restrict__ P, C* __restrict__ T) {
+    const long long nout = (long long)r * k;
+    const long long tot = lv.t0[lv.nlev] * nout;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long tb = e / nout;
+        const int oi = (int)(e - tb * nout);
+        int q = 0;
+        while (q + 1 < lv.nlev && tb >= lv.t0[q + 1]) ++q;
+        const int j = (int)(tb - lv.t0[q]);
+        const int per = lv.nb[q] / lv.ch[q];
+        const C* p = P + ((long long)lv.chunk0[q] + (long long)j * per) * nout + oi;
+        C s = czero<C>();
+        for (int u = 0; u < per; ++u) s = cadd(s, p[(long long)u * nout]);
+        T[e] = s;
+    }
+}
+
+// Y[i][c] += sum over levels of G_b'(row) T_b' for k <= 64 columns: thread
+// (row, group of 16 columns); T is read through the cache (uniform across a
+// warp's lanes).
+template <typename C>
+__global__ void __launch_bounds__(256)
+k_lr_apply(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ T, int swapC, C* __restrict__ Y) {
+    const int ngrp = (k + 15) / 16;
+    const int rows_per = 256 / ngrp;
+    const int lr = threadIdx.x % rows_per, g = threadIdx.x / rows_per;
+    if (g >= ngrp) return;
+    const int i = blockIdx.x * rows_per + lr;
+    if (i >= m) return;
+    const int c0 = g * 16;
+    const long long nout = (long long)r * k;
+    C acc[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc[t] = czero<C>();
+    for (int q = 0; q < lv.nlev; ++q) {
+        const int nb = lv.nb[q];
+        const int b = i / nb, o = i - b * nb;
+        const int bb = swapC ? (b ^ 1) : b;
+        const C* Gb = lv.G[q] + (long long)bb * nb * r + o;
+        const C* Tb = T + (lv.t0[q] + bb) * nout;
+        for (int t = 0; t < r; ++t) {
+            const C gv = Gb[(long long)t * nb];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (c0 + u < k) cfma(acc[u], gv, Tb[(long long)(c0 + u) * r + t]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+        if (c0 + u < k) {
+            C* y = Y + (long long)(c0 + u) * m + i;
+            *y = cadd(*y, acc[u]);
+        }
+}
+
+// Levels l+1..L of node (l, c): F and G are U or W (see the callers).
+template <typename R>
+lsw_status lr_levels(const HStore<R>& H, int l, int c, bool F_is_W, const typename Cx<R>::T* X, int k,
+                     typename Cx<R>::T* Y, int swapA, int swapC, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    const int L = H.L, r = H.r, m = H.nl(l);
+    if (L - l > kMaxLev) return LSW_ERR_UNSUPPORTED_SIZE;
+    if (L <= l) return LSW_OK;
+    if (r * k > 4096 || k > 64) return LSW_ERR_INVALID_ARG;
+    LrLevels<C> lv;
+    lv.nlev = L - l;
+    lv.chunk0[0] = 0;
+    lv.t0[0] = 0;
+    for (int q = 0; q < lv.nlev; ++q) {
+        const int lp = l + 1 + q, cnt = 1 << (lp - l), nb = H.nl(lp);
+        const size_t first = (size_t)c * cnt;
+        const C* U0 = H.U[lp] + first * nb * r;
+        const C* W0 = H.W[lp] + first * nb * r;
+        lv.F[q] = F_is_W ? W0 : U0;
+        lv.G[q] = F_is_W ? U0 : W0;
+        lv.nb[q] = nb;
+        lv.ch[q] = std::min(nb, 256);
+        lv.chunk0[q + 1] = lv.chunk0[q] + m / lv.ch[q];
+        lv.t0[q + 1] = lv.t0[q] + cnt;
+    }
+    for (int q = lv.nlev; q < kMaxLev; ++q) {
+        lv.F[q] = lv.G[q] = nullptr;
+        lv.nb[q] = lv.ch[q] = 1;
+        lv.chunk0[q + 1] = lv.chunk0[q];
+        lv.t0[q + 1] = lv.t0[q];
+    }
+    const long long nout = (long long)r * k;
+    DevBuf P, T;
+    LSW_TRY(P.alloc(sizeof(C) * (size_t)lv.chunk0[lv.nlev] * nout, st));
+    LSW_TRY(T.alloc(sizeof(C) * (size_t)lv.t0[lv.nlev] * nout, st));
+    static std::atomic<bool> attr[2];
+    if (!attr[sizeof(R) == 8]) {
+        LSW_CUDA(cudaFuncSetAttribute(k_lr_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        attr[sizeof(R) == 8] = true;
+    }
+    k_lr_partial<C><<<lv.chunk0[lv.nlev], 256, sizeof(C) * 33 * (r + k), st>>>(lv, m, r, k, X, swapA, P.as<C>());
+    LSW_LAUNCH_CHECK();
+    k_lr_reduce<C><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
+    LSW_LAUNCH_CHECK();
+    const int rows_per = 256 / ((k + 15) / 16);
+    k_lr_apply<C><<<(m + rows_per - 1) / rows_per, 256, 0, st>>>(lv, m, r, k, T.as<C>(), swapC, Y);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
 // Y = X_sub * Xin for node (l, c) (k columns, ld = n_l); T: workspace of
-// 2^(L-l) * r * k complex.
+// 2^(L-l) * r * k complex (used by the per-level path for k > 64).
 template <typename R>
 lsw_status hmv(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X, int k, typename Cx<R>::T* Y,
                typename Cx<R>::T* T, cudaStream_t st) {
@@ -434,12 +615,13 @@ lsw_status hmv(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X, int
     const int nleaf = 1 << (L - l);
     const C* D0 = H.D + (size_t)c * nleaf * nL * nL;
     LSW_TRY(gemm<R>('N', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st));
+    // T_j = W_j^H X[sibling rows];  Y[rows j] += U_j T_j
+    if (k <= 64 && r * k <= 4096) return lr_levels<R>(H, l, c, true, X, k, Y, 1, 0, st);
     for (int lp = l + 1; lp <= L; ++lp) {
         const int cnt = 1 << (lp - l), nb = H.nl(lp);
         const size_t first = (size_t)c * cnt;
         const C* U0 = H.U[lp] + first * nb * r;
         const C* W0 = H.W[lp] + first * nb * r;
-        // T_j = W_j^H X[sibling rows]
         LSW_TRY(gemm<R>('C', 'N', r, k, nb, one<C>(), W0, nb, 2LL * nb * r, X + nb, m, 2LL * nb, zero<C>(), T, r,
                         2LL * r * k, cnt / 2, st));
         LSW_TRY(gemm<R>('C', 'N', r, k, nb, one<C>(), W0 + (size_t)nb * r, nb, 2LL * nb * r, X, m, 2LL * nb, zero<C>(),
@@ -459,12 +641,13 @@ lsw_status hmv_adj(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X,
     const int nleaf = 1 << (L - l);
     const C* D0 = H.D + (size_t)c * nleaf * nL * nL;
     LSW_TRY(gemm<R>('C', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st));
+    // T_j = U_j^H X[rows j];  Y[rows j ^ 1] += W_j T_j
+    if (k <= 64 && r * k <= 4096) return lr_levels<R>(H, l, c, false, X, k, Y, 0, 1, st);
     for (int lp = l + 1; lp <= L; ++lp) {
         const int cnt = 1 << (lp - l), nb = H.nl(lp);
         const size_t first = (size_t)c * cnt;
         const C* U0 = H.U[lp] + first * nb * r;
         const C* W0 = H.W[lp] + first * nb * r;
-        // T_j = U_j^H X[rows j];  Y[rows j^1] += W_j T_j
         LSW_TRY(gemm<R>('C', 'N', r, k, nb, one<C>(), U0, nb, (long long)nb * r, X, m, nb, zero<C>(), T, r,
                         (long long)r * k, cnt, st));
         LSW_TRY(gemm<R>('N', 'N', nb, k, r, one<C>(), W0, nb, 2LL * nb * r, T, r, 2LL * r * k, one<C>(), Y + nb, m,

@@ -1407,26 +1407,39 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
     if (batch <= 0 || k <= 0 || m <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
     (void)work;
-    constexpr int NT = 512;
-    const size_t cap = 200 * 1024;
-    int cmax = (int)std::min<size_t>(1024, (cap / sizeof(CT) - (size_t)k * k) / k);
+    // Two chunk shapes: 512 threads on up to ~200 KB of rows (one CTA per
+    // SM), or 128 threads on <= 256 rows (three CTAs per SM).  The column
+    // loop of a chunk is latency-bound, so small chunks are chosen whenever
+    // the large ones would leave the GPU's 152 SMs short of three CTAs each.
+    const size_t capL = 200 * 1024, capS = 72 * 1024;
+    const int cmaxL = (int)std::min<size_t>(1024, (capL / sizeof(CT) - (size_t)k * k) / k);
+    const int cmaxS = (int)std::min<size_t>(256, (capS / sizeof(CT) - (size_t)k * k) / k);
     static std::atomic<bool> attr[2];
     if (!attr[sizeof(R) == 8]) {
-        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_chunk<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_apply<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_chunk<R, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)capL));
+        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_apply<R, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)capL));
+        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_chunk<R, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)capS));
+        LSW_CUDA(cudaFuncSetAttribute(k_tsqr_apply<R, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)capS));
         attr[sizeof(R) == 8] = true;
     }
+    const long long nchL = (m + cmaxL - 1) / cmaxL;
+    const bool small = cmaxS >= 2 * k && (m <= cmaxS || nchL * batch < 3LL * 152);
+    const int cmax = small ? cmaxS : cmaxL;
     // Tall-skinny QR (TSQR): factor row chunks independently, then the
     // stacked R factors, then combine.  Every chunk has >= cmax/2 >= k rows.
     const int nch = (m + cmax - 1) / cmax;
     const int rows = (m + nch - 1) / nch;
     const size_t smem = sizeof(CT) * ((size_t)rows * k + (size_t)k * k);
+    auto chunk = [&](int nc, CT* S) {
+        if (small) k_tsqr_chunk<R, 128><<<dim3(nc, batch), 128, smem, st>>>(A, m, k, sA, nc, S);
+        else k_tsqr_chunk<R, 512><<<dim3(nc, batch), 512, smem, st>>>(A, m, k, sA, nc, S);
+    };
     if (nch == 1) {
         DevBuf S;
         LSW_TRY(S.alloc(sizeof(CT) * (size_t)batch * k * k, st));
         KTimer kt("qr", st, sizeof(CT) * ((double)batch * m * k * 2 + (double)batch * k * k),
                   16.0 * batch * (double)m * k * k);
-        k_tsqr_chunk<R, NT><<<dim3(1, batch), NT, smem, st>>>(A, m, k, sA, 1, S.as<CT>());
+        chunk(1, S.as<CT>());
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
@@ -1438,11 +1451,12 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
         // explicit Q: 16 m k^2 real flops per block (8 each)
         KTimer kt("qr", st, sizeof(CT) * ((double)batch * m * k * 2 + (double)batch * ms * k),
                   16.0 * batch * (double)m * k * k);
-        k_tsqr_chunk<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
+        chunk(nch, S.as<CT>());
         LSW_LAUNCH_CHECK();
     }
     LSW_TRY(qr_explicit<R>(S.as<CT>(), ms, k, (long long)ms * k, batch, nullptr, st));
-    k_tsqr_apply<R, NT><<<dim3(nch, batch), NT, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
+    if (small) k_tsqr_apply<R, 128><<<dim3(nch, batch), 128, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
+    else k_tsqr_apply<R, 512><<<dim3(nch, batch), 512, smem, st>>>(A, m, k, sA, nch, S.as<CT>());
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
