@@ -124,8 +124,9 @@ uint64_t lsw_launch_count(void);
  * method).  lsw_kernel_timer_start(family) resets and enables it for
  * "operator_c64" / "operator_c128" (the three FFT passes of one operator
  * apply in that precision), "qr" (the row
- * chunks of the tall-skinny QR) or "gj_update" (the Gauss-Jordan block
- * updates); CUDA events are then recorded on the launching stream around
+ * chunks of the tall-skinny QR), "gj_update" (the Gauss-Jordan block
+ * updates) or "leaf_tc" (the tensor-core products of H's dense leaves);
+ * CUDA events are then recorded on the launching stream around
  * each such launch, with the algorithmic bytes and flops of its work.
  * lsw_kernel_timer_read waits for the recorded events and reports the sums
  * (any pointer may be NULL). */
@@ -277,6 +278,14 @@ lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hpar
  * Synchronises the stream. */
 lsw_status lsw_autotune(const lsw_green* g, int prec, int nbatch, void* stream,
                         int* variant, float* ms3);
+
+/* Process-wide switch (default on) for the tensor-core path of the FP32
+ * products of H's dense leaves with blocks of up to 32 vectors (tcgen05,
+ * three TF32 products per real product, FP32 accumulation: results agree
+ * with the CUDA-core path to FP32 rounding, not bit for bit).  Off: every
+ * product runs on the CUDA cores.  Not part of the method; for A/B
+ * comparisons and reproducibility across paths. */
+lsw_status lsw_set_tensor_cores(int enable);
 
 /* ------------------------------------------------------------------------
  * Learned right preconditioner.  The paper has no network: its Sec. 3.2

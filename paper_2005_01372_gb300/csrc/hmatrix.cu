@@ -446,13 +446,21 @@ template <typename C> struct LrLevels {
     int nlev;
 };
 
+// Partial T over one chunk of CH rows: out (r x k) = F_chunk^H X_chunk.
+// Rows go through shared memory in tiles of 32, stored row-major so that a
+// thread reads 2 x 2 complex at a time; thread (microtile, row group) keeps a
+// 4 x 4 block of outputs over every G-th row of the tile, and the row groups
+// are summed in shared memory at the end.
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int swapA, C* __restrict__ P) {
     constexpr int TR = 32;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    C (*Fs)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw);            // r rows
-    C (*Xs)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw) + r;        // k rows
+    const int rs = (r + 3) & ~3, ks = (k + 3) & ~3;       // columns rounded up to 4
+    const int fsd = rs + 1, xsd = ks + 1;                 // odd row strides: conflict-free transposing stores
+    C* Fs = reinterpret_cast<C*>(sm_raw);                 // TR x fsd
+    C* Xs = Fs + TR * fsd;                                // TR x xsd
+    C* Red = Xs + TR * xsd;                               // G x r x k
     int q = 0;
     while (q + 1 < lv.nlev && (int)blockIdx.x >= lv.chunk0[q + 1]) ++q;
     const int chn = blockIdx.x - lv.chunk0[q];
@@ -460,41 +468,58 @@ k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int s
     const int row0 = chn * CH;
     const int j = row0 / nb, o = row0 - j * nb;
     const int src = swapA ? (j ^ 1) : j;
-    const C* Fj = lv.F[q] + (long long)j * nb * r;
-    const C* Xs_g = X + (long long)src * nb + o;
-    const int nout = r * k;
-    C acc[16];
+    const C* Fj = lv.F[q] + (long long)j * nb * r + o;
+    const C* Xg = X + (long long)src * nb + o;
+    const int mtr = rs / 4, mtk = ks / 4, nmt = mtr * mtk;
+    const int G = max(1, 256 / nmt);
+    const int mt = threadIdx.x % nmt, rg = threadIdx.x / nmt;
+    const bool active = rg < G;
+    const int t0 = (mt % mtr) * 4, c0 = (mt / mtr) * 4;
+    C acc[4][4];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) acc[t] = czero<C>();
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = czero<C>();
     for (int r0 = 0; r0 < CH; r0 += TR) {
         const int nr = min(TR, CH - r0);
-        for (int e = threadIdx.x; e < TR * r; e += 256) {
+        for (int e = threadIdx.x; e < TR * rs; e += 256) {
             const int cc = e / TR, rr = e - cc * TR;
-            Fs[cc][rr] = rr < nr ? Fj[(long long)cc * nb + o + r0 + rr] : czero<C>();
+            Fs[rr * fsd + cc] = (rr < nr && cc < r) ? Fj[(long long)cc * nb + r0 + rr] : czero<C>();
         }
-        for (int e = threadIdx.x; e < TR * k; e += 256) {
+        for (int e = threadIdx.x; e < TR * ks; e += 256) {
             const int cc = e / TR, rr = e - cc * TR;
-            Xs[cc][rr] = rr < nr ? Xs_g[(long long)cc * m + r0 + rr] : czero<C>();
+            Xs[rr * xsd + cc] = (rr < nr && cc < k) ? Xg[(long long)cc * m + r0 + rr] : czero<C>();
         }
         __syncthreads();
+        if (active) {
+            for (int rr = rg; rr < nr; rr += G) {
+                C f[4], x[4];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const int oi = threadIdx.x + 256 * t;
-            if (oi < nout) {
-                const int i = oi % r, jj = oi / r;
-                C sacc = acc[t];
-#pragma unroll 8
-                for (int rr = 0; rr < TR; ++rr) cfmac(sacc, Fs[i][rr], Xs[jj][rr]);
-                acc[t] = sacc;
+                for (int a = 0; a < 4; ++a) f[a] = Fs[rr * fsd + t0 + a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) x[b] = Xs[rr * xsd + c0 + b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) cfmac(acc[a][b], f[a], x[b]);
             }
         }
         __syncthreads();
     }
-    C* out = P + (long long)blockIdx.x * nout;
+    const int nout = r * k;
+    if (active) {
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-        const int oi = threadIdx.x + 256 * t;
-        if (oi < nout) out[oi] = acc[t];
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (t0 + a < r && c0 + b < k) Red[(long long)rg * nout + (c0 + b) * r + t0 + a] = acc[a][b];
+    }
+    __syncthreads();
+    C* out = P + (long long)blockIdx.x * nout;
+    for (int e = threadIdx.x; e < nout; e += 256) {
+        C sacc = czero<C>();
+        for (int g = 0; g < G; ++g) sacc = cadd(sacc, Red[(long long)g * nout + e]);
+        out[e] = sacc;
     }
 }
 
@@ -517,42 +542,59 @@ __global__ void k_lr_reduce(LrLevels<C> lv, int r, int k, const C* __restrict__ 
     }
 }
 
-// Y[i][c] += sum over levels of G_b'(row) T_b' for k <= 64 columns: thread
-// (row, group of 16 columns); T is read through the cache (uniform across a
-// warp's lanes).
+// Y[i][c] += sum over levels of G_b'(row) T_b': thread (4 consecutive rows,
+// group of 8 columns); the 4 rows share their block at every level (block
+// sizes are multiples of 4), so each T entry loaded serves 4 rows.
 template <typename C>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_lr_apply(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ T, int swapC, C* __restrict__ Y) {
-    const int ngrp = (k + 15) / 16;
-    const int rows_per = 256 / ngrp;
-    const int lr = threadIdx.x % rows_per, g = threadIdx.x / rows_per;
+    const int ngrp = (k + 7) / 8;
+    const int slots = 128 / ngrp;
+    const int slot = threadIdx.x % slots, g = threadIdx.x / slots;
     if (g >= ngrp) return;
-    const int i = blockIdx.x * rows_per + lr;
-    if (i >= m) return;
-    const int c0 = g * 16;
+    const int i0 = (blockIdx.x * slots + slot) * 4;
+    if (i0 >= m) return;
+    const int c0 = g * 8;
     const long long nout = (long long)r * k;
-    C acc[16];
+    C acc[4][8];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) acc[t] = czero<C>();
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[a][u] = czero<C>();
     for (int q = 0; q < lv.nlev; ++q) {
         const int nb = lv.nb[q];
-        const int b = i / nb, o = i - b * nb;
+        const int b = i0 / nb, o = i0 - b * nb;
         const int bb = swapC ? (b ^ 1) : b;
         const C* Gb = lv.G[q] + (long long)bb * nb * r + o;
         const C* Tb = T + (lv.t0[q] + bb) * nout;
         for (int t = 0; t < r; ++t) {
-            const C gv = Gb[(long long)t * nb];
+            C gv[4], tv[8];
 #pragma unroll
-            for (int u = 0; u < 16; ++u)
-                if (c0 + u < k) cfma(acc[u], gv, Tb[(long long)(c0 + u) * r + t]);
+            for (int a = 0; a < 4; ++a) gv[a] = Gb[(long long)t * nb + a];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) tv[u] = c0 + u < k ? Tb[(long long)(c0 + u) * r + t] : czero<C>();
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cfma(acc[a][u], gv[a], tv[u]);
         }
     }
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
+    for (int u = 0; u < 8; ++u)
         if (c0 + u < k) {
-            C* y = Y + (long long)(c0 + u) * m + i;
-            *y = cadd(*y, acc[u]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                C* y = Y + (long long)(c0 + u) * m + i0 + a;
+                *y = cadd(*y, acc[a][u]);
+            }
         }
+}
+
+// Shapes the fused kernels take: k <= 64 columns, rank <= 64, r k <= 4096,
+// block sizes (hence node sizes) multiples of 4.
+template <typename R>
+bool lr_fused_ok(const HStore<R>& H, int l, int k) {
+    return k >= 1 && k <= 64 && H.r <= 64 && H.r * k <= 4096 && (H.nl(H.L) & 3) == 0 && H.L - l <= kMaxLev;
 }
 
 // Levels l+1..L of node (l, c): F and G are U or W (see the callers).
@@ -563,7 +605,7 @@ lsw_status lr_levels(const HStore<R>& H, int l, int c, bool F_is_W, const typena
     const int L = H.L, r = H.r, m = H.nl(l);
     if (L - l > kMaxLev) return LSW_ERR_UNSUPPORTED_SIZE;
     if (L <= l) return LSW_OK;
-    if (r * k > 4096 || k > 64) return LSW_ERR_INVALID_ARG;
+    if (r * k > 4096 || k > 64 || r > 64 || (m & 3)) return LSW_ERR_INVALID_ARG;
     LrLevels<C> lv;
     lv.nlev = L - l;
     lv.chunk0[0] = 0;
@@ -592,17 +634,38 @@ lsw_status lr_levels(const HStore<R>& H, int l, int c, bool F_is_W, const typena
     LSW_TRY(T.alloc(sizeof(C) * (size_t)lv.t0[lv.nlev] * nout, st));
     static std::atomic<bool> attr[2];
     if (!attr[sizeof(R) == 8]) {
-        LSW_CUDA(cudaFuncSetAttribute(k_lr_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        LSW_CUDA(cudaFuncSetAttribute(k_lr_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr[sizeof(R) == 8] = true;
     }
-    k_lr_partial<C><<<lv.chunk0[lv.nlev], 256, sizeof(C) * 33 * (r + k), st>>>(lv, m, r, k, X, swapA, P.as<C>());
+    const int rs = (r + 3) & ~3, ks = (k + 3) & ~3;
+    const int Gr = std::max(1, 256 / ((rs / 4) * (ks / 4)));
+    const size_t smem = sizeof(C) * (32 * (size_t)(rs + ks + 2) + (size_t)Gr * r * k);
+    k_lr_partial<C><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
     LSW_LAUNCH_CHECK();
     k_lr_reduce<C><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
     LSW_LAUNCH_CHECK();
-    const int rows_per = 256 / ((k + 15) / 16);
-    k_lr_apply<C><<<(m + rows_per - 1) / rows_per, 256, 0, st>>>(lv, m, r, k, T.as<C>(), swapC, Y);
+    const int rows_cta = 4 * (128 / ((k + 7) / 8));
+    k_lr_apply<C><<<(m + rows_cta - 1) / rows_cta, 128, 0, st>>>(lv, m, r, k, T.as<C>(), swapC, Y);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
+}
+
+// Y_b = D_b X_b for nleaf consecutive dense leaves (nL x nL each) and k
+// columns (X, Y: ld m): on the tensor cores in FP32 when the shape allows.
+template <typename R>
+lsw_status leaf_product(const typename Cx<R>::T* D0, int nL, const typename Cx<R>::T* X, int m, int k,
+                        typename Cx<R>::T* Y, int nleaf, cudaStream_t st) {
+    typedef typename Cx<R>::T C;
+    return gemm<R>('N', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st);
+}
+
+template <>
+lsw_status leaf_product<float>(const float2* D0, int nL, const float2* X, int m, int k, float2* Y, int nleaf,
+                               cudaStream_t st) {
+    if (tc_gemm_enabled() && tc_gemm_fits(nL, k, nL))
+        return cgemm_tc(D0, nL, (long long)nL * nL, X, m, nL, Y, m, nL, nL, k, nL, make_float2(1.f, 0.f), nleaf, st);
+    return gemm<float>('N', 'N', nL, k, nL, one<float2>(), D0, nL, (long long)nL * nL, X, m, nL, zero<float2>(), Y, m,
+                       nL, nleaf, st);
 }
 
 // Y = X_sub * Xin for node (l, c) (k columns, ld = n_l); T: workspace of
@@ -614,9 +677,9 @@ lsw_status hmv(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X, int
     const int m = H.nl(l), L = H.L, r = H.r, nL = H.nl(L);
     const int nleaf = 1 << (L - l);
     const C* D0 = H.D + (size_t)c * nleaf * nL * nL;
-    LSW_TRY(gemm<R>('N', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st));
+    LSW_TRY(leaf_product<R>(D0, nL, X, m, k, Y, nleaf, st));
     // T_j = W_j^H X[sibling rows];  Y[rows j] += U_j T_j
-    if (k <= 64 && r * k <= 4096) return lr_levels<R>(H, l, c, true, X, k, Y, 1, 0, st);
+    if (lr_fused_ok(H, l, k)) return lr_levels<R>(H, l, c, true, X, k, Y, 1, 0, st);
     for (int lp = l + 1; lp <= L; ++lp) {
         const int cnt = 1 << (lp - l), nb = H.nl(lp);
         const size_t first = (size_t)c * cnt;
@@ -642,7 +705,7 @@ lsw_status hmv_adj(const HStore<R>& H, int l, int c, const typename Cx<R>::T* X,
     const C* D0 = H.D + (size_t)c * nleaf * nL * nL;
     LSW_TRY(gemm<R>('C', 'N', nL, k, nL, one<C>(), D0, nL, (long long)nL * nL, X, m, nL, zero<C>(), Y, m, nL, nleaf, st));
     // T_j = U_j^H X[rows j];  Y[rows j ^ 1] += W_j T_j
-    if (k <= 64 && r * k <= 4096) return lr_levels<R>(H, l, c, false, X, k, Y, 0, 1, st);
+    if (lr_fused_ok(H, l, k)) return lr_levels<R>(H, l, c, false, X, k, Y, 0, 1, st);
     for (int lp = l + 1; lp <= L; ++lp) {
         const int cnt = 1 << (lp - l), nb = H.nl(lp);
         const size_t first = (size_t)c * cnt;

@@ -213,6 +213,15 @@ lsw_status gaussian_fill(typename Cx<R>::T* dst, int m, int k, long long sD, int
 template <typename R>
 lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cudaStream_t st);
 
+// Batched complex FP32 GEMM C_b = alpha A_b B_b on the tcgen05 tensor cores
+// (3xTF32, FP32 accuracy), column-major, for M % 128 == 0, K % 16 == 0,
+// 1 <= N <= 32 (tc_gemm.cu).  tc_gemm_enabled: the process-wide switch.
+bool tc_gemm_enabled();
+void tc_gemm_enable(bool on);
+bool tc_gemm_fits(int M, int N, int K);
+lsw_status cgemm_tc(const float2* A, int lda, long long sA, const float2* B, int ldb, long long sB, float2* C, int ldc,
+                    long long sC, int M, int N, int K, float2 alpha, int batch, cudaStream_t st);
+
 // Per-field FP64 squared 2-norms: out[b] = sum |x_b|^2 over n entries.
 template <typename R>
 lsw_status norms2(const typename Cx<R>::T* x, long long n, int batch, double* out, cudaStream_t st);

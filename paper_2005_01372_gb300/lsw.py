@@ -99,6 +99,7 @@ _SIGS = {
     "lsw_solve_batched": (I32, [VP, I32, ctypes.POINTER(_HParams), ctypes.POINTER(_SolveParams), I32,
                                 ctypes.POINTER(SolveInfo), VP]),
     "lsw_autotune": (I32, [VP, I32, I32, VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "lsw_set_tensor_cores": (I32, [I32]),
     "lsw_fno_create": (I32, [ctypes.POINTER(_FnoParams), VP, ctypes.POINTER(VP)]),
     "lsw_fno_destroy": (I32, [VP]),
     "lsw_fno_num_params": (I32, [VP, ctypes.POINTER(ctypes.c_int64)]),
@@ -255,6 +256,11 @@ def kernel_timer_read():
 
 def kernel_timer_stop():
     _check(lib().lsw_kernel_timer_stop(), "lsw_kernel_timer_stop")
+
+
+def set_tensor_cores(enable: bool):
+    """Process-wide switch for the tensor-core products of H's dense leaves."""
+    _check(lib().lsw_set_tensor_cores(1 if enable else 0), "lsw_set_tensor_cores")
 
 
 def build_green(nz, nx, h, c0, freq_hz, stream=None) -> Green:

@@ -220,3 +220,30 @@ def test_zero_contrast_series(lsw):
     u, infos = lsw.solve_series(G, chi, H, u0, sp=lsw.SolveParams(prec=lsw.C128, tol=1e-12))
     assert infos[0].iterations == 0 and infos[0].status == 0
     assert torch.equal(u, u0)
+
+
+@pytest.mark.parametrize("n,L,k", [(64, 2, 32), (64, 2, 7), (128, 3, 20)])
+def test_tensor_core_leaf_products_match_cuda_cores(lsw, n, L, k):
+    """The tcgen05 products of the dense leaves (three TF32 products per
+    real product, FP32 accumulation in tensor memory) agree with the
+    CUDA-core path to 5e-5: each term carries ~2^-21 relative error and the
+    leaf inverses' cancellation amplifies it about tenfold, while a single
+    TF32 product (the lo terms lost) would be off by ~5e-4.  Both agree
+    with the oracle's H to its FP32 tolerance."""
+    P, G, chi = _setup(lsw, n, n, seed=17, freq=12.0)
+    H = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=L, rank=12, oversample=6,
+                                              seed=41))
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(media.complex_field(rng, (k, n * n)).astype(np.complex64)).cuda()
+    try:
+        lsw.set_tensor_cores(True)
+        y_tc = lsw.apply_precond(H, x).cpu().numpy()
+        lsw.set_tensor_cores(False)
+        y_cc = lsw.apply_precond(H, x).cpu().numpy()
+    finally:
+        lsw.set_tensor_cores(True)
+    assert np.all(np.isfinite(y_tc))
+    assert _rel(y_tc, y_cc) < 5e-5
+    ref = oh.HODLRPreconditioner(P, L, 12, 6, 0, 41)
+    want = ref.apply(x.cpu().numpy().astype(np.complex128).T).T
+    assert _rel(y_tc, want) < 1e-4
