@@ -48,7 +48,7 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
     const int kbeg = kp * kchunk, kend = min(k, kbeg + kchunk);
     const C* Ab = A + b * sA;
     const C* Bb = B + b * sB;
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int ty = threadIdx.x % TY, tx = threadIdx.x / TY;   // consecutive lanes: consecutive rows (coalesced C)
     C acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1122,7 +1122,7 @@ k_gj_update_oop(const C* __restrict__ Ain, C* __restrict__ Aout, int n, long lon
     if (threadIdx.x < 64) rmap[threadIdx.x] = i0 + threadIdx.x < n ? sigma(i0 + threadIdx.x) : 0;
     if (threadIdx.x < 16) pmap[threadIdx.x] = threadIdx.x < nb ? sigma(k0 + threadIdx.x) : 0;
     __syncthreads();
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int ty = threadIdx.x & 15, tx = threadIdx.x >> 4;   // consecutive lanes: consecutive rows
     C acc[4][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -1190,7 +1190,7 @@ k_gj_update(C* __restrict__ Aall, int n, long long sA, int k0, int nb, const C* 
     C* A = Aall + b * sA;
     const C* XP = XPall + (long long)b * nb * n;
     const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int ty = threadIdx.x & 15, tx = threadIdx.x >> 4;   // consecutive lanes: consecutive rows
     C acc[4][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
