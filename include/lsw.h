@@ -128,6 +128,9 @@ uint64_t lsw_launch_count(void);
  * updates) or "leaf_tc" (the tensor-core products of H's dense leaves);
  * CUDA events are then recorded on the launching stream around
  * each such launch, with the algorithmic bytes and flops of its work.
+ * Phases of lsw_build_hmatrix (HODLR) time the same way, on the stream that
+ * runs them: "hodlr_level_sketch" (one level's sketches), "hodlr_leaf_inverse"
+ * (the dense leaves' inverses) and "hodlr_invert" (the recursive inversion).
  * lsw_kernel_timer_read waits for the recorded events and reports the sums
  * (any pointer may be NULL). */
 lsw_status lsw_kernel_timer_start(const char* family);

@@ -887,19 +887,29 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
         const int4 P0 = tr.node(l - 1, 0);
         LSW_TRY(build_spectrum(g, P0.y - P0.x, P0.w - P0.z, &spec[l], st));
     }
+    const int nL = tr.nl(L);
     {
-        // the levels are independent: sketch them concurrently
+        // the levels are independent of each other and of the dense leaves:
+        // sketch every level and invert every original leaf concurrently
+        // (the inversion's Schur-complement leaves then follow by Woodbury
+        // from these inverses)
         Fork fk(st);
-        for (int l = 1; l <= L; ++l)
-            LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, spec[l], fk.child(l)));
+        for (int l = 1; l <= L; ++l) {
+            cudaStream_t sl = fk.child(l);
+            KTimer kt("hodlr_level_sketch", sl, 0, 0);
+            LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, spec[l], sl));
+        }
+        cudaStream_t sd = fk.child(0);
+        {
+            KTimer kt("hodlr_leaf_inverse", sd, 0, 0);
+            k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, sd>>>(g->table, g->nz, chi, h->perm_d, nL, 1 << L,
+                                                                           X.D);
+            LSW_LAUNCH_CHECK();
+            LSW_TRY(inverse_gj<R>(X.D, nL, (long long)nL * nL, 1 << L, sd));
+        }
         LSW_TRY(fk.join());
     }
-    const int nL = tr.nl(L);
-    k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, st>>>(g->table, g->nz, chi, h->perm_d, nL, 1 << L, X.D);
-    LSW_LAUNCH_CHECK();
-    // every original leaf inverted at once; the inversion's Schur-complement
-    // leaves then follow by Woodbury from these
-    LSW_TRY(inverse_gj<R>(X.D, nL, (long long)nL * nL, 1 << L, st));
+    KTimer kti("hodlr_invert", st, 0, 0);
     LeafUpd<R> lu;
     lu.nL = nL;
     lu.kmax = std::max(1, r * L);

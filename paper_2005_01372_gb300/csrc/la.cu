@@ -987,11 +987,13 @@ k_gj_panel(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* __res
 // every row by the scaled pivot row -- four barriers per column.
 template <typename C, int NT, int NB>
 __global__ void __launch_bounds__(NT)
-k_gj_panel_reg(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* __restrict__ pivall) {
+k_gj_panel_reg(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* __restrict__ pivall,
+               int* __restrict__ swlall) {
     typedef decltype(Aall->x) R;
     __shared__ R wbest[NT / 32];
     __shared__ int widx[NT / 32];
     __shared__ int pivrow;
+    __shared__ int pvs[NB];
     __shared__ C rowc[NB];
     __shared__ C xbuf[2][NB];
     C* A = Aall + blockIdx.x * sA;
@@ -1026,6 +1028,7 @@ k_gj_panel_reg(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* _
             if (i == 0) {
                 pivrow = i2 < n ? i2 : c;
                 piv[c] = pivrow;
+                pvs[j] = pivrow;
             }
         }
         __syncthreads();
@@ -1079,6 +1082,25 @@ k_gj_panel_reg(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* _
         for (int t = 0; t < NB; ++t)
             if (t < nb) A[(long long)(k0 + t) * n + i] = prow[t];
     }
+    // the panel's interchanges composed into one permutation sigma of the
+    // positions they touch (count, then position/value pairs), for the update
+    if (i == 0) {
+        int* swl = swlall + (long long)blockIdx.x * (4 * NB + 1);
+        int cnt = 0;
+        for (int j = 0; j < nb; ++j) {
+            const int c = k0 + j, p = pvs[j];
+            if (p == c) continue;
+            int ic = -1, ip = -1;
+            for (int q = 0; q < cnt; ++q) {
+                if (swl[1 + 2 * q] == c) ic = q;
+                if (swl[1 + 2 * q] == p) ip = q;
+            }
+            if (ic < 0) { swl[1 + 2 * cnt] = c; swl[2 + 2 * cnt] = c; ic = cnt++; }
+            if (ip < 0) { swl[1 + 2 * cnt] = p; swl[2 + 2 * cnt] = p; ip = cnt++; }
+            const int t = swl[2 + 2 * ic]; swl[2 + 2 * ic] = swl[2 + 2 * ip]; swl[2 + 2 * ip] = t;
+        }
+        swl[0] = cnt;
+    }
 }
 
 // Out-of-place block step for every column outside the panel, with the
@@ -1088,7 +1110,7 @@ k_gj_panel_reg(C* __restrict__ Aall, int n, long long sA, int k0, int nb, int* _
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_gj_update_oop(const C* __restrict__ Ain, C* __restrict__ Aout, int n, long long sA, int k0, int nb,
-                const int* __restrict__ pivall) {
+                const int* __restrict__ swlall, int swstride) {
     __shared__ C Ps[64][17];
     __shared__ C Xs[16][65];
     __shared__ int rmap[64];
@@ -1098,21 +1120,16 @@ k_gj_update_oop(const C* __restrict__ Ain, C* __restrict__ Aout, int n, long lon
     const int b = blockIdx.z;
     const C* A = Ain + b * sA;
     C* O = Aout + b * sA;
-    const int* piv = pivall + (long long)b * n;
     const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
-    if (threadIdx.x == 0) {
-        // sigma on the positions the swaps touch
-        int cnt = 0;
-        for (int j = 0; j < nb; ++j) {
-            const int c = k0 + j, p = piv[c];
-            if (p == c) continue;
-            int ic = -1, ip = -1;
-            for (int q = 0; q < cnt; ++q) { if (sw_pos[q] == c) ic = q; if (sw_pos[q] == p) ip = q; }
-            if (ic < 0) { sw_pos[cnt] = c; sw_val[cnt] = c; ic = cnt++; }
-            if (ip < 0) { sw_pos[cnt] = p; sw_val[cnt] = p; ip = cnt++; }
-            const int t = sw_val[ic]; sw_val[ic] = sw_val[ip]; sw_val[ip] = t;
+    {
+        // sigma on the positions the panel's swaps touch, composed by the panel kernel
+        const int* swl = swlall + (long long)b * swstride;
+        const int cnt = swl[0];
+        if (threadIdx.x == 0) nsw = cnt;
+        if (threadIdx.x < cnt) {
+            sw_pos[threadIdx.x] = swl[1 + 2 * threadIdx.x];
+            sw_val[threadIdx.x] = swl[2 + 2 * threadIdx.x];
         }
-        nsw = cnt;
     }
     __syncthreads();
     auto sigma = [&](int pos) {
@@ -1534,21 +1551,23 @@ lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cuda
         // register panels + out-of-place updates, ping-pong between A and B
         constexpr int NB = sizeof(R) == 8 ? 8 : 16;
         const int nb = NB;
-        DevBuf piv, B;
+        DevBuf piv, B, swl;
         LSW_TRY(piv.alloc(sizeof(int) * (size_t)n * batch, st));
         LSW_TRY(B.alloc(sizeof(CT) * (size_t)sA * batch, st));
+        const int swstride = 4 * NB + 1;
+        LSW_TRY(swl.alloc(sizeof(int) * (size_t)swstride * batch, st));
         CT* cur = A;
         CT* nxt = B.as<CT>();
         for (int k0 = 0; k0 < n; k0 += nb) {
             const int w = std::min(nb, n - k0);
-            k_gj_panel_reg<CT, NT, NB><<<batch, NT, 0, st>>>(cur, n, sA, k0, w, piv.as<int>());
+            k_gj_panel_reg<CT, NT, NB><<<batch, NT, 0, st>>>(cur, n, sA, k0, w, piv.as<int>(), swl.as<int>());
             LSW_LAUNCH_CHECK();
             if (w == n) continue;
             {
                 // reads and writes every matrix once; 8 n^2 w real flops each
                 KTimer kt("gj_update", st, 2.0 * sizeof(CT) * (double)n * n * batch, 8.0 * (double)n * n * w * batch);
                 k_gj_update_oop<CT><<<dim3((n + 63) / 64, (n + 63) / 64, batch), 256, 0, st>>>(cur, nxt, n, sA, k0, w,
-                                                                                              piv.as<int>());
+                                                                                              swl.as<int>(), swstride);
                 LSW_LAUNCH_CHECK();
             }
             std::swap(cur, nxt);
