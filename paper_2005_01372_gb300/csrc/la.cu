@@ -621,10 +621,17 @@ k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long s
 }
 
 // --------------------------------------------- Jacobi eigen (Hermitian)
+// A pair (p, q) is rotated only while |a_pq| > t sqrt(|a_pp a_qq|), t a few
+// units of rounding of the working precision; a sweep that rotates nothing
+// ends the iteration (the classical threshold rule, which terminates even
+// when rounding keeps the off-diagonal norm above a fixed fraction).
+template <typename R> __device__ __forceinline__ R jacobi_skip() { return sizeof(R) == 8 ? (R)1e-14 : (R)1e-6; }
+
 // Parallel cyclic Jacobi in precision R: each round rotates k/2 disjoint
 // index pairs chosen by the circle method, so every pair is met once per
 // sweep.  Input: FP64 Hermitian G (k x k), scaled by its trace; output: the
 // eigenvectors as columns of V, by decreasing eigenvalue.
+#define JACOBI_COUNT_ROTATION atomicAdd(&nrot, 1)
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k) {
@@ -638,6 +645,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     __shared__ C red[33];
     __shared__ double trs;
     __shared__ int order[64];
+    __shared__ int nrot;
     const double2* G = Gall + (long long)blockIdx.x * k * k;
     if (threadIdx.x == 0) {
         double t = 0;
@@ -663,6 +671,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
         }
         const C on = block_sum<C, 256>(part, red);
         if (!(on.x > tol * on.y) || on.y == 0) break;
+        if (threadIdx.x == 0) nrot = 0;
         for (int r = 0; r < m - 1; ++r) {
             for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
                 int p, q;
@@ -674,7 +683,11 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                     const R app = A[p * k + p].x, aqq = A[q * k + q].x;
                     const C c = A[q * k + p];   // A[p][q]
                     const R ac = sqrt(c.x * c.x + c.y * c.y);
-                    if (ac > (R)1e-30 * (fabs(app) + fabs(aqq)) && ac > 0) {
+                    // rotate only while the pair is not yet negligible
+                    // against its diagonal (relative threshold above rounding)
+                    if (ac > jacobi_skip<R>() * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
+                        ac > 0) {
+                        JACOBI_COUNT_ROTATION;
                         const R tau = (aqq - app) / (2 * ac);
                         const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
                         cs = (R)1 / sqrt((R)1 + t * t);
@@ -718,6 +731,8 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
             }
             __syncthreads();
         }
+        if (nrot == 0) break;          // a sweep without a rotation: converged
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         for (int i = 0; i < k; ++i) order[i] = i;
@@ -738,6 +753,8 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
 
 // The same Jacobi iteration with one warp per matrix (k <= 64) and several
 // matrices per CTA: lanes share the work of a round, __syncwarp orders it.
+#undef JACOBI_COUNT_ROTATION
+#define JACOBI_COUNT_ROTATION ++nrw
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int batch) {
@@ -781,6 +798,7 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
             tot += __shfl_xor_sync(0xffffffffu, tot, o);
         }
         if (!(off > tol * tot) || tot == 0) break;
+        int nrw = 0;
         for (int r = 0; r < m - 1; ++r) {
             for (int i = lane; i < m / 2; i += 32) {
                 int p, q;
@@ -792,7 +810,11 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
                     const R app = A[p * k + p].x, aqq = A[q * k + q].x;
                     const C c = A[q * k + p];
                     const R ac = sqrt(c.x * c.x + c.y * c.y);
-                    if (ac > (R)1e-30 * (fabs(app) + fabs(aqq)) && ac > 0) {
+                    // rotate only while the pair is not yet negligible
+                    // against its diagonal (relative threshold above rounding)
+                    if (ac > jacobi_skip<R>() * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
+                        ac > 0) {
+                        JACOBI_COUNT_ROTATION;
                         const R tau = (aqq - app) / (2 * ac);
                         const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
                         cs = (R)1 / sqrt((R)1 + t * t);
@@ -833,7 +855,9 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
             }
             __syncwarp();
         }
+        if (!__any_sync(0xffffffffu, nrw)) break;    // a sweep without a rotation: converged
     }
+#undef JACOBI_COUNT_ROTATION
     if (lane == 0) {
         for (int i = 0; i < k; ++i) order[i] = i;
         for (int i = 0; i < k; ++i) {
@@ -1140,6 +1164,22 @@ k_gj_update_oop(const C* __restrict__ Ain, C* __restrict__ Aout, int n, long lon
     if (threadIdx.x < 16) pmap[threadIdx.x] = threadIdx.x < nb ? sigma(k0 + threadIdx.x) : 0;
     __syncthreads();
     const int ty = threadIdx.x & 15, tx = threadIdx.x >> 4;   // consecutive lanes: consecutive rows
+    // the old entries this thread's outputs add to, requested before the
+    // panel product so that their latency overlaps it
+    C aold[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int li = ty + 16 * p;
+            const int gi = i0 + li, gj = j0 + tx + 16 * q;
+            C v = czero<C>();
+            if (gi < n && gj < n) {
+                if (gj >= k0 && gj < k0 + nb) v = A[(long long)gj * n + gi];
+                else if (!(gi >= k0 && gi < k0 + nb)) v = A[(long long)gj * n + rmap[li]];
+            }
+            aold[p][q] = v;
+        }
     C acc[4][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -1172,9 +1212,9 @@ k_gj_update_oop(const C* __restrict__ Ain, C* __restrict__ Aout, int n, long lon
             const int gi = i0 + li, gj = j0 + tx + 16 * q;
             if (gi >= n || gj >= n) continue;
             C* o = O + (long long)gj * n + gi;
-            if (gj >= k0 && gj < k0 + nb) { *o = A[(long long)gj * n + gi]; continue; }
-            if (gi >= k0 && gi < k0 + nb) *o = acc[p][q];
-            else *o = cadd(A[(long long)gj * n + rmap[li]], acc[p][q]);
+            if (gj >= k0 && gj < k0 + nb) *o = aold[p][q];
+            else if (gi >= k0 && gi < k0 + nb) *o = acc[p][q];
+            else *o = cadd(aold[p][q], acc[p][q]);
         }
 }
 
