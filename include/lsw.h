@@ -130,7 +130,10 @@ uint64_t lsw_launch_count(void);
  * each such launch, with the algorithmic bytes and flops of its work.
  * Phases of lsw_build_hmatrix (HODLR) time the same way, on the stream that
  * runs them: "hodlr_level_sketch" (one level's sketches), "hodlr_leaf_inverse"
- * (the dense leaves' inverses) and "hodlr_invert" (the recursive inversion).
+ * (the dense leaves' inverses), "hodlr_invert" (the recursive inversion) and,
+ * inside it, "hodlr_add_lowrank" (one low-rank update with its
+ * recompressions), "hodlr_leaf_woodbury" (one Schur leaf) and
+ * "hodlr_subtree_products" (a pair of subtree products).
  * lsw_kernel_timer_read waits for the recorded events and reports the sums
  * (any pointer may be NULL). */
 lsw_status lsw_kernel_timer_start(const char* family);

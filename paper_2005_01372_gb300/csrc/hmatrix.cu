@@ -122,6 +122,10 @@ template <typename R> struct LeafUpd {
     C* U = nullptr;   // nleaf x nL x kmax
     C* V = nullptr;
     int nL = 0, kmax = 0;
+    // the original leaves' inverses arrive in batches on another stream:
+    // leaves [end[b-1], end[b]) are ready once ready[b] has fired
+    std::vector<cudaEvent_t> ready;
+    std::vector<int> end;
 };
 
 }  // namespace lsw
@@ -727,6 +731,7 @@ template <typename R>
 lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, const typename Cx<R>::T* Y, int op,
                        int call_l, int call_c, int oversample, uint64_t seed, cudaStream_t st0,
                        LeafUpd<R>* lu = nullptr) {
+    KTimer kt_all("hodlr_add_lowrank", st0, 0, 0);
     cudaStream_t st = st0;
     typedef typename Cx<R>::T C;
     const int m = M.nl(l), L = M.L, r = M.r, nL = M.nl(L);
@@ -801,6 +806,12 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
         //   S^-1 = D^-1 - D^-1 U (I + V^H D^-1 U)^-1 V^H D^-1.
         const int nL = X.nl(L);
         const long long nn = (long long)nL * nL;
+        for (size_t b = 0; b < lu.end.size(); ++b)
+            if (c < lu.end[b]) {
+                LSW_CUDA(cudaStreamWaitEvent(st, lu.ready[b], 0));
+                break;
+            }
+        KTimer kt_leaf("hodlr_leaf_woodbury", st, 0, 0);
         const C* Di = X.D + (size_t)c * nn;
         C* d = Hi.D + (size_t)c * nn;
         LSW_CUDA(cudaMemcpyAsync(d, Di, sizeof(C) * nn, cudaMemcpyDeviceToDevice, st));
@@ -841,15 +852,21 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
     LSW_TRY(XK.alloc(vb, st));
     LSW_TRY(K.alloc(sizeof(C) * r * r, st));
     LSW_TRY(T.alloc(sizeof(C) * ((size_t)1 << (L - l)) * r * r, st));
-    LSW_TRY(hmv<R>(Hi, l + 1, a, UB, r, P.as<C>(), T.as<C>(), st));        // P = A^-1 UB
-    LSW_TRY(hmv_adj<R>(Hi, l + 1, a, WC, r, Rm.as<C>(), T.as<C>(), st));   // R = A^-H WC
+    {
+        KTimer kt_sub("hodlr_subtree_products", st, 0, 0);
+        LSW_TRY(hmv<R>(Hi, l + 1, a, UB, r, P.as<C>(), T.as<C>(), st));        // P = A^-1 UB
+        LSW_TRY(hmv_adj<R>(Hi, l + 1, a, WC, r, Rm.as<C>(), T.as<C>(), st));   // R = A^-H WC
+    }
     LSW_TRY(gemm<R>('C', 'N', r, r, m1, one<C>(), WC, m1, 0, P.as<C>(), m1, 0, zero<C>(), K.as<C>(), r, 0, 1, st));
     // S = D - UC K WB^H  (in place on X's node b)
     LSW_TRY(gemm<R>('N', 'N', m1, r, r, minus_one<C>(), UC, m1, 0, K.as<C>(), r, 0, zero<C>(), XK.as<C>(), m1, 0, 1, st));
     LSW_TRY(add_lowrank<R>(X, l + 1, b, XK.as<C>(), WB, 0, l, c, oversample, seed, st, &lu));
     LSW_TRY(invert_node<R>(X, l + 1, b, Hi, oversample, seed, st, lu));     // S^-1 into Hi
-    LSW_TRY(hmv<R>(Hi, l + 1, b, UC, r, T1.as<C>(), T.as<C>(), st));       // T1 = S^-1 UC
-    LSW_TRY(hmv_adj<R>(Hi, l + 1, b, WB, r, T2.as<C>(), T.as<C>(), st));   // T2 = S^-H WB
+    {
+        KTimer kt_sub("hodlr_subtree_products", st, 0, 0);
+        LSW_TRY(hmv<R>(Hi, l + 1, b, UC, r, T1.as<C>(), T.as<C>(), st));       // T1 = S^-1 UC
+        LSW_TRY(hmv_adj<R>(Hi, l + 1, b, WB, r, T2.as<C>(), T.as<C>(), st));   // T2 = S^-H WB
+    }
     LSW_TRY(gemm<R>('C', 'N', r, r, m1, one<C>(), WB, m1, 0, T1.as<C>(), m1, 0, zero<C>(), K.as<C>(), r, 0, 1, st));
     // top-left: A^-1 + P K2 R^H
     LSW_TRY(gemm<R>('N', 'N', m1, r, r, one<C>(), P.as<C>(), m1, 0, K.as<C>(), r, 0, zero<C>(), XK.as<C>(), m1, 0, 1, st));
@@ -888,29 +905,53 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
         LSW_TRY(build_spectrum(g, P0.y - P0.x, P0.w - P0.z, &spec[l], st));
     }
     const int nL = tr.nl(L);
+    const int nleaf = 1 << L;
+    LeafUpd<R> lu;
+    struct EvGuard {
+        std::vector<cudaEvent_t>* v;
+        ~EvGuard() { for (auto e : *v) cudaEventDestroy(e); }
+    } evguard{&lu.ready};
+    // The original leaves are inverted on their own stream, in batches in
+    // the order the recursive inversion first needs them (leaf 0 first): the
+    // first eighth, the next eighth, the next quarter, the last half.  Each
+    // batch fires an event that the inversion waits on before its first use
+    // of a leaf of that batch, so later batches overlap the inversion.
+    {
+        const int b0 = std::max(1, nleaf / 8);
+        for (int e = b0; e < nleaf; e *= 2) lu.end.push_back(e);
+        lu.end.push_back(nleaf);
+        for (size_t b = 0; b < lu.end.size(); ++b) {
+            cudaEvent_t ev;
+            LSW_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            lu.ready.push_back(ev);
+        }
+    }
+    Fork fkd(st);
+    {
+        cudaStream_t sd = fkd.child(0);
+        KTimer kt("hodlr_leaf_inverse", sd, 0, 0);
+        k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, sd>>>(g->table, g->nz, chi, h->perm_d, nL, nleaf, X.D);
+        LSW_LAUNCH_CHECK();
+        int first = 0;
+        for (size_t b = 0; b < lu.end.size(); ++b) {
+            const long long nn = (long long)nL * nL;
+            LSW_TRY(inverse_gj<R>(X.D + (size_t)first * nn, nL, nn, lu.end[b] - first, sd));
+            LSW_CUDA(cudaEventRecord(lu.ready[b], sd));
+            first = lu.end[b];
+        }
+    }
     {
         // the levels are independent of each other and of the dense leaves:
-        // sketch every level and invert every original leaf concurrently
-        // (the inversion's Schur-complement leaves then follow by Woodbury
-        // from these inverses)
+        // sketch them concurrently
         Fork fk(st);
         for (int l = 1; l <= L; ++l) {
             cudaStream_t sl = fk.child(l);
             KTimer kt("hodlr_level_sketch", sl, 0, 0);
             LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, spec[l], sl));
         }
-        cudaStream_t sd = fk.child(0);
-        {
-            KTimer kt("hodlr_leaf_inverse", sd, 0, 0);
-            k_leaf_assemble<C><<<gridn((long long)tr.n * nL), 256, 0, sd>>>(g->table, g->nz, chi, h->perm_d, nL, 1 << L,
-                                                                           X.D);
-            LSW_LAUNCH_CHECK();
-            LSW_TRY(inverse_gj<R>(X.D, nL, (long long)nL * nL, 1 << L, sd));
-        }
         LSW_TRY(fk.join());
     }
     KTimer kti("hodlr_invert", st, 0, 0);
-    LeafUpd<R> lu;
     lu.nL = nL;
     lu.kmax = std::max(1, r * L);
     DevBuf ub, vb;
@@ -923,6 +964,7 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
     lu.V = vb.as<C>();
     LSW_TRY(Hi.alloc(L, r, tr.n));
     LSW_TRY(invert_node<R>(X, 0, 0, Hi, hp->oversample, hp->seed, st, lu));
+    LSW_TRY(fkd.join());
     LSW_CUDA(cudaStreamSynchronize(st));
     return LSW_OK;
 }

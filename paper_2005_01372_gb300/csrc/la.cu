@@ -1582,11 +1582,125 @@ lsw_status gaussian_fill(typename Cx<R>::T* dst, int m, int k, long long sD, int
     return LSW_OK;
 }
 
+// Gauss-Jordan inverse of one small matrix (n <= GJS_MAX) per CTA, held in
+// shared memory (column-major, leading dimension n + 1): for every column,
+// pick the largest pivot below the diagonal, swap it up, scale its row and
+// eliminate the column from every other row; the column swaps that undo the
+// row interchanges come last.  Same pivoting as the blocked path.
+template <typename C>
+__global__ void __launch_bounds__(512)
+k_gj_small(C* __restrict__ Aall, int n, long long sA) {
+    typedef decltype(Aall->x) R;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int ld = n + 1;
+    C* A = reinterpret_cast<C*>(sm_raw);              // n x ld
+    C* rowj = A + (size_t)n * ld;                      // n
+    C* colj = rowj + n;                                // n
+    int* piv = reinterpret_cast<int*>(colj + n);       // n
+    __shared__ R wbest[16];
+    __shared__ int widx[16];
+    __shared__ int pivrow;
+    __shared__ C pval;
+    C* G = Aall + blockIdx.x * sA;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int c = e / n, i = e - c * n;
+        A[c * ld + i] = G[e];
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        // pivot: largest |A(i, j)|, i >= j (lowest index on ties)
+        R best = (R)-1;
+        int bi = n;
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+            const C a = A[j * ld + i];
+            const R v = a.x * a.x + a.y * a.y;
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { wbest[threadIdx.x >> 5] = best; widx[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int nw = blockDim.x >> 5;
+            R b2 = threadIdx.x < nw ? wbest[threadIdx.x] : (R)-1;
+            int i2 = threadIdx.x < nw ? widx[threadIdx.x] : n;
+            for (int o = 16; o > 0; o >>= 1) {
+                const R ob = __shfl_xor_sync(0xffffffffu, b2, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, i2, o);
+                if (ob > b2 || (ob == b2 && oi < i2)) { b2 = ob; i2 = oi; }
+            }
+            if (threadIdx.x == 0) {
+                pivrow = i2 < n ? i2 : j;
+                piv[j] = pivrow;
+                pval = A[j * ld + pivrow];
+            }
+        }
+        __syncthreads();
+        const int p = pivrow;
+        // swap rows j and p; keep the scaled pivot row and the old column j
+        const C d = pval;
+        const R den = d.x * d.x + d.y * d.y;
+        const C inv = den > 0 ? mk(d.x / den, -d.y / den) : czero<C>();
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const C aj = A[c * ld + j], ap = A[c * ld + p];
+            A[c * ld + p] = aj;
+            rowj[c] = c == j ? inv : cmul(ap, inv);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) colj[i] = i == j ? czero<C>() : A[j * ld + i];
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int c = e / n, i = e - c * n;
+            if (i == j) {
+                A[c * ld + i] = rowj[c];
+            } else {
+                const C f = colj[i];
+                const C rj = rowj[c];
+                A[c * ld + i] = c == j ? mk(-(f.x * rj.x - f.y * rj.y), -(f.x * rj.y + f.y * rj.x))
+                                       : csub(A[c * ld + i], cmul(f, rj));
+            }
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int j = n - 1; j >= 0; --j) {
+        const int p = piv[j];
+        if (p != j)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const C t = A[j * ld + i];
+                A[j * ld + i] = A[p * ld + i];
+                A[p * ld + i] = t;
+            }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int c = e / n, i = e - c * n;
+        G[e] = A[c * ld + i];
+    }
+}
+
 template <typename R>
 lsw_status inverse_gj(typename Cx<R>::T* A, int n, long long sA, int batch, cudaStream_t st) {
     typedef typename Cx<R>::T CT;
     if (n <= 0 || batch <= 0) return LSW_OK;
     constexpr int NT = 1024;
+    {
+        // small matrices: one CTA each, entirely in shared memory
+        const size_t smem = sizeof(CT) * ((size_t)n * (n + 1) + 2 * (size_t)n) + sizeof(int) * (size_t)n;
+        if (n <= 160 && smem <= 200 * 1024) {
+            static std::atomic<bool> attrs[2];
+            if (!attrs[sizeof(R) == 8]) {
+                LSW_CUDA(cudaFuncSetAttribute(k_gj_small<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+                attrs[sizeof(R) == 8] = true;
+            }
+            k_gj_small<CT><<<batch, 512, smem, st>>>(A, n, sA);
+            LSW_LAUNCH_CHECK();
+            return LSW_OK;
+        }
+    }
     if (n <= NT) {
         // register panels + out-of-place updates, ping-pong between A and B
         constexpr int NB = sizeof(R) == 8 ? 8 : 16;
