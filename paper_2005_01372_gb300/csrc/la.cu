@@ -131,53 +131,74 @@ k_gemm(int opA, int opB, int m, int n, int k, C alpha, const C* __restrict__ A, 
 
 // C = A^H B partial sums for small outputs (m, n <= 64) and long K: CTA
 // (kpart, b) takes rows [k0, k1) of A (K x m) and B (K x n) in tiles of 32
-// rows through shared memory; thread t owns output entries t, t+256, ...
+// rows through shared memory, stored row-major with odd strides (conflict-
+// free transposing stores).  Thread (microtile, row group) keeps a 4 x 4
+// block of outputs over every G-th row of a tile; the row groups are summed
+// in shared memory at the end.
 template <typename C>
 __global__ void __launch_bounds__(256)
 k_gemm_cn_small(int m, int n, int k, const C* __restrict__ A, int lda, long long sA, const C* __restrict__ B, int ldb,
                 long long sB, int kchunk, C* __restrict__ P, int batch) {
     constexpr int TR = 32;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    C (*As)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw);            // m rows
-    C (*Bs)[TR + 1] = reinterpret_cast<C (*)[TR + 1]>(sm_raw) + m;        // n rows
+    const int ms = (m + 3) & ~3, ns = (n + 3) & ~3;
+    const int asd = ms + 1, bsd = ns + 1;
+    C* As = reinterpret_cast<C*>(sm_raw);         // TR x asd
+    C* Bs = As + TR * asd;                         // TR x bsd
+    C* Red = Bs + TR * bsd;                        // G x m x n
     const int kp = blockIdx.x, b = blockIdx.y;
     const int k0 = kp * kchunk, k1 = min(k, k0 + kchunk);
     const C* Ab = A + b * sA;
     const C* Bb = B + b * sB;
-    const int nout = m * n;
-    C acc[16];
+    const int mtr = ms / 4, mtn = ns / 4, nmt = mtr * mtn;
+    const int G = max(1, 256 / nmt);
+    const int mt = threadIdx.x % nmt, rg = threadIdx.x / nmt;
+    const bool active = rg < G;
+    const int i0 = (mt % mtr) * 4, j0 = (mt / mtr) * 4;
+    C acc[4][4];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = czero<C>();
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = czero<C>();
     for (int r0 = k0; r0 < k1; r0 += TR) {
         const int nr = min(TR, k1 - r0);
-        for (int e = threadIdx.x; e < TR * m; e += 256) {
-            const int c = e / TR, r = e - c * TR;
-            As[c][r] = r < nr ? Ab[(long long)c * lda + r0 + r] : czero<C>();
+        for (int e = threadIdx.x; e < TR * ms; e += 256) {
+            const int cc = e / TR, rr = e - cc * TR;
+            As[rr * asd + cc] = (rr < nr && cc < m) ? Ab[(long long)cc * lda + r0 + rr] : czero<C>();
         }
-        for (int e = threadIdx.x; e < TR * n; e += 256) {
-            const int c = e / TR, r = e - c * TR;
-            Bs[c][r] = r < nr ? Bb[(long long)c * ldb + r0 + r] : czero<C>();
+        for (int e = threadIdx.x; e < TR * ns; e += 256) {
+            const int cc = e / TR, rr = e - cc * TR;
+            Bs[rr * bsd + cc] = (rr < nr && cc < n) ? Bb[(long long)cc * ldb + r0 + rr] : czero<C>();
         }
         __syncthreads();
+        if (active) {
+            for (int rr = rg; rr < nr; rr += G) {
+                C x[4], y[4];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int o = threadIdx.x + 256 * q;
-            if (o < nout) {
-                const int i = o % m, j = o / m;
-                C s = acc[q];
-                for (int r = 0; r < TR; ++r) cfmac(s, As[i][r], Bs[j][r]);
-                acc[q] = s;
+                for (int a = 0; a < 4; ++a) x[a] = As[rr * asd + i0 + a];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) y[c] = Bs[rr * bsd + j0 + c];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cfmac(acc[a][c], x[a], y[c]);
             }
         }
         __syncthreads();
     }
+    const int nout = m * n;
+    if (active) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int o = threadIdx.x + 256 * q;
-        if (o < nout) {
-            const int i = o % m, j = o / m;
-            P[(((long long)kp * batch + b) * n + j) * m + i] = acc[q];
-        }
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (i0 + a < m && j0 + c < n) Red[(long long)rg * nout + (j0 + c) * m + i0 + a] = acc[a][c];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nout; e += 256) {
+        C sacc = czero<C>();
+        for (int g = 0; g < G; ++g) sacc = cadd(sacc, Red[(long long)g * nout + e]);
+        P[((long long)kp * batch + b) * nout + e] = sacc;
     }
 }
 
@@ -1350,6 +1371,13 @@ __global__ void k_cast64(const double2* __restrict__ s, C* __restrict__ d, long 
 }  // namespace
 
 // ================================================================ wrappers
+template <typename CT>
+size_t cn_small_smem(int m, int n) {
+    const int ms = (m + 3) & ~3, ns = (n + 3) & ~3;
+    const int G = std::max(1, 256 / ((ms / 4) * (ns / 4)));
+    return sizeof(CT) * (32 * (size_t)(ms + ns + 2) + (size_t)G * m * n);
+}
+
 template <typename R>
 lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha,
                 const typename Cx<R>::T* A, int lda, long long sA,
@@ -1396,10 +1424,10 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
         LSW_TRY(part.alloc(sizeof(CT) * (size_t)ksplit * batch * m * n, st));
         static std::atomic<bool> attr_cn[2];
         if (!attr_cn[sizeof(R) == 8]) {
-            LSW_CUDA(cudaFuncSetAttribute(k_gemm_cn_small<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            LSW_CUDA(cudaFuncSetAttribute(k_gemm_cn_small<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
             attr_cn[sizeof(R) == 8] = true;
         }
-        k_gemm_cn_small<CT><<<dim3(ksplit, batch), 256, sizeof(CT) * 33 * (m + n), st>>>(m, n, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(),
+        k_gemm_cn_small<CT><<<dim3(ksplit, batch), 256, cn_small_smem<CT>(m, n), st>>>(m, n, k, A, lda, sA, B, ldb, sB, kchunk, part.as<CT>(),
                                                                    batch);
         LSW_LAUNCH_CHECK();
         k_gemm_reduce<CT><<<grid_for((long long)batch * m * n), 256, 0, st>>>(m, n, batch, ksplit, part.as<CT>(), alpha,
@@ -1652,15 +1680,17 @@ k_gj_small(C* __restrict__ Aall, int n, long long sA) {
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) colj[i] = i == j ? czero<C>() : A[j * ld + i];
         __syncthreads();
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int c = e / n, i = e - c * n;
-            if (i == j) {
-                A[c * ld + i] = rowj[c];
-            } else {
-                const C f = colj[i];
-                const C rj = rowj[c];
-                A[c * ld + i] = c == j ? mk(-(f.x * rj.x - f.y * rj.y), -(f.x * rj.y + f.y * rj.x))
-                                       : csub(A[c * ld + i], cmul(f, rj));
+        // threads as 32 rows x 16 columns: lanes on consecutive rows, no division
+        for (int c = threadIdx.x >> 5; c < n; c += 16) {
+            const C rj = rowj[c];
+            for (int i = threadIdx.x & 31; i < n; i += 32) {
+                if (i == j) {
+                    A[c * ld + i] = rj;
+                } else {
+                    const C f = colj[i];
+                    A[c * ld + i] = c == j ? mk(-(f.x * rj.x - f.y * rj.y), -(f.x * rj.y + f.y * rj.x))
+                                           : csub(A[c * ld + i], cmul(f, rj));
+                }
             }
         }
         __syncthreads();
