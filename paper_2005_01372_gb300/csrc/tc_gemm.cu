@@ -14,7 +14,7 @@
 //
 // One CTA of 128 threads owns 128 rows of one matrix.  Per stage of 16
 // complex K (32 real): every thread loads its row of A and a slice of B into
-// registers one stage ahead, splits them and stores hi/lo tiles into shared
+// registers two stages ahead, splits them and stores hi/lo tiles into shared
 // memory in the canonical K-major layout without swizzle (8-row x 16-byte core
 // matrices, 128 B apart along K, 1024 B apart along rows); one thread issues
 // 3 x 4 tcgen05.mma of 128 x 64 x 8 and commits them to the stage's mbarrier,
@@ -134,8 +134,9 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
 
     const int S = K / TC_KC;
     const int jb = lane, gb = warp;              // B slice: column jb, complex k 4 gb .. 4 gb + 3
-    float2 ra[TC_KC], rb[4];
-    auto gload = [&](int s) {
+    // two register sets, each loaded two stages ahead of its use
+    float2 ra0[TC_KC], rb0[4], ra1[TC_KC], rb1[4];
+    auto gload = [&](int s, float2 (&ra)[TC_KC], float2 (&rb)[4]) {
         const int k0 = s * TC_KC;
 #pragma unroll
         for (int kk = 0; kk < TC_KC; ++kk) ra[kk] = Ab[(long long)(k0 + kk) * lda + tid];
@@ -143,9 +144,10 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
         for (int q = 0; q < 4; ++q)
             rb[q] = jb < N ? Bb[(long long)jb * ldb + k0 + 4 * gb + q] : make_float2(0.f, 0.f);
     };
-    gload(0);
     int committed = 0;
-    for (int s = 0; s < S; ++s) {
+    // one stage: wait for the buffer, split and store, refill the register
+    // set for stage s + 2, issue the MMAs; false when a wait gave up
+    auto stage = [&](int s, float2 (&ra)[TC_KC], float2 (&rb)[4]) -> bool {
         const int buf = s & 1;
         unsigned char* Ahi = sm + buf * STAGE;
         unsigned char* Alo = Ahi + A_TILE;
@@ -153,7 +155,7 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
         unsigned char* Blo = Bhi + B_TILE;
         if (tid == 0 && s >= 2 && !mbar_wait(buf ? mb1 : mb0, ((s - 2) >> 1) & 1)) *abort_flag = 1;
         __syncthreads();
-        if (*abort_flag) break;
+        if (*abort_flag) return false;
         // A'' row tid: kgroup q holds [Re a(2q), Im a(2q), Re a(2q+1), Im a(2q+1)]
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -182,7 +184,7 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (s + 1 < S) gload(s + 1);           // next stage's loads overlap this stage's MMAs
+        if (s + 2 < S) gload(s + 2, ra, rb);    // two stages of loads stay in flight
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
@@ -196,6 +198,13 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
             mma_commit(buf ? mb1 : mb0);
         }
         committed = s + 1;
+        return true;
+    };
+    gload(0, ra0, rb0);
+    if (S > 1) gload(1, ra1, rb1);
+    for (int s = 0; s < S; s += 2) {
+        if (!stage(s, ra0, rb0)) break;
+        if (s + 1 < S && !stage(s + 1, ra1, rb1)) break;
     }
     // the last commit covers every MMA issued before it
     if (tid == 0 && committed > 0) {
