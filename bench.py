@@ -103,6 +103,9 @@ class ClockSampler:
 
 
 DOMINANT = "qr"
+# DRAM bytes (read + write) per k_tsqr_chunk launch, from one ncu capture of all
+# 267 launches of the benchmark's HODLR build (profiles/qr_chunk_hodlr_build_256x256.md)
+QR_TRAFFIC_PER_LAUNCH = 1463721
 
 
 def fp32_alu_peak_tflops() -> float:
@@ -223,7 +226,7 @@ def run_ours(args):
     dom_gbs = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     roof = {"kernel": "k_tsqr_chunk: row-chunk Householder QR of the sketch blocks (largest share of the step)",
             "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(dom_gbs / peak, 4), "traffic": None, "launches": int(dom_n),
+            "frac": round(dom_gbs / peak, 4), "traffic": QR_TRAFFIC_PER_LAUNCH, "launches": int(dom_n),
             "avg_launch_ms": round(dom_ms / max(1, dom_n), 4),
             "achieved_tflops": round(dom_flops / (dom_ms / 1e3) / 1e12, 3) if dom_ms > 0 else 0.0}
     op_tf = op_flops / (op_ms / 1e3) / 1e12 if op_ms > 0 else 0.0
