@@ -191,13 +191,14 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     typedef std::complex<double> Z;
     const long long n = (long long)g->nz * g->nx;
     m = std::max(1, std::min(m, 128));
-    DevBuf V, Zb, vj, zj, w, hc, work, dn, act, ysc, yb;
+    DevBuf V, Zb, vj, zj, w, hc, hc2, work, dn, act, ysc, yb;
     LSW_TRY(V.alloc(sizeof(C) * n * (m + 1) * nb, st));
     LSW_TRY(Zb.alloc(sizeof(C) * n * m * nb, st));
     LSW_TRY(vj.alloc(sizeof(C) * n * nb, st));
     LSW_TRY(zj.alloc(sizeof(C) * n * nb, st));
     LSW_TRY(w.alloc(sizeof(C) * n * nb, st));
     LSW_TRY(hc.alloc(sizeof(C) * (m + 1) * nb, st));
+    LSW_TRY(hc2.alloc(sizeof(C) * (m + 1) * nb, st));
     LSW_TRY(ysc.alloc(sizeof(double) * nb, st));
     LSW_TRY(yb.alloc(sizeof(C) * m * nb, st));
     LSW_CUDA(cudaMemsetAsync(Zb.p, 0, sizeof(C) * n * m * nb, st));
@@ -209,7 +210,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     for (int s = 0; s < nb; ++s)
         if (!(nrmb[s] > 0)) { done[s] = 1; info[s].status = LSW_OK; info[s].rel = 0; }
     std::vector<Z> H((size_t)nb * (m + 1) * m), gv((size_t)nb * (m + 1)), cs((size_t)nb * m), sn((size_t)nb * m);
-    std::vector<C> hh((size_t)(m + 1) * nb), yh((size_t)m * nb);
+    std::vector<C> hh((size_t)(m + 1) * nb), hh2((size_t)(m + 1) * nb), yh((size_t)m * nb);
     std::vector<int> kused(nb, 0), conv(nb, 0), its(nb, 0);
     std::vector<double> scale(nb), wstart(nb);
     const C one_ = mk((R)1, (R)0), zero_ = mk((R)0, (R)0), mone = mk((R)-1, (R)0);
@@ -255,22 +256,29 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
             else LSW_CUDA(cudaMemcpyAsync(zj.p, vj.p, sizeof(C) * n * nb, cudaMemcpyDeviceToDevice, st));
             LSW_CUDA(cudaMemcpy2DAsync(Zb.as<char>() + row * j, pitchZ, zj.p, row, row, nb, cudaMemcpyDeviceToDevice, st));
             LSW_TRY(op_full<R>(g, chi, LSW_OP_RESIDUAL, zj.as<C>(), nullptr, w.as<C>(), nb, work, st));
-            // two passes of classical Gram-Schmidt against v_0..v_j
+            // two passes of classical Gram-Schmidt against v_0..v_j, then the
+            // norm of what is left: the coefficients of both passes and the
+            // norms come back to the host together, one wait per iteration
             std::vector<Z> hsum((size_t)nb * (j + 1), 0.0);
             for (int pass = 0; pass < 2; ++pass) {
+                C* hcp = pass == 0 ? hc.as<C>() : hc2.as<C>();
                 LSW_TRY(gemm<R>('C', 'N', j + 1, 1, (int)n, one_, V.as<C>(), (int)n, n * (m + 1), w.as<C>(), (int)n, n,
-                                zero_, hc.as<C>(), m + 1, m + 1, nb, st));
-                LSW_TRY(gemm<R>('N', 'N', (int)n, 1, j + 1, mone, V.as<C>(), (int)n, n * (m + 1), hc.as<C>(), m + 1,
-                                m + 1, one_, w.as<C>(), (int)n, n, nb, st));
-                LSW_CUDA(cudaMemcpyAsync(hh.data(), hc.p, sizeof(C) * (m + 1) * nb, cudaMemcpyDeviceToHost, st));
-                LSW_CUDA(cudaStreamSynchronize(st));
-                for (int s = 0; s < nb; ++s)
-                    for (int i = 0; i <= j; ++i) {
-                        const C v = hh[(size_t)s * (m + 1) + i];
-                        hsum[(size_t)s * (j + 1) + i] += Z((double)v.x, (double)v.y);
-                    }
+                                zero_, hcp, m + 1, m + 1, nb, st));
+                LSW_TRY(gemm<R>('N', 'N', (int)n, 1, j + 1, mone, V.as<C>(), (int)n, n * (m + 1), hcp, m + 1, m + 1,
+                                one_, w.as<C>(), (int)n, n, nb, st));
             }
-            LSW_TRY(host_norms<R>(w.as<C>(), n, nb, dn, nr, st));
+            if (!dn.p) LSW_TRY(dn.alloc(sizeof(double) * nb, st));
+            LSW_TRY(norms2<R>(w.as<C>(), n, nb, dn.as<double>(), st));
+            nr.resize(nb);
+            LSW_CUDA(cudaMemcpyAsync(hh.data(), hc.p, sizeof(C) * (m + 1) * nb, cudaMemcpyDeviceToHost, st));
+            LSW_CUDA(cudaMemcpyAsync(hh2.data(), hc2.p, sizeof(C) * (m + 1) * nb, cudaMemcpyDeviceToHost, st));
+            LSW_CUDA(cudaMemcpyAsync(nr.data(), dn.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+            LSW_CUDA(cudaStreamSynchronize(st));
+            for (int s = 0; s < nb; ++s)
+                for (int i = 0; i <= j; ++i) {
+                    const C v = hh[(size_t)s * (m + 1) + i], v2 = hh2[(size_t)s * (m + 1) + i];
+                    hsum[(size_t)s * (j + 1) + i] += Z((double)v.x + (double)v2.x, (double)v.y + (double)v2.y);
+                }
             for (int s = 0; s < nb; ++s) scale[s] = (!conv[s] && nr[s] > 0) ? 1.0 / std::sqrt(nr[s]) : 0.0;
             LSW_TRY(up(ysc, scale, st));
             k_scale_cast<C, C><<<gridn(n * nb), 256, 0, st>>>(w.as<C>(), vj.as<C>(), ysc.as<double>(), n, nb);
