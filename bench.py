@@ -122,6 +122,20 @@ def op_bytes_c64(n: int, nsrc: int) -> float:
     return 24.0 * n * nsrc + 8.0 * n + 8.0 * (nz + 1) * (nx + 1)
 
 
+def reduce_over_ranks(ms_local: float, solves_local: float, device):
+    """Whole-job timing of the replicas: the slowest rank's time and the sum of
+    every rank's converged solves (each rank solves its own copy of the
+    workload; these two scalars are the only collectives)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    c = torch.tensor([float(solves_local)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -190,14 +204,7 @@ def run_ours(args):
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    ms = float(np.sum(times))
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    c = torch.tensor([conv], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    solves = float(c.item())
+    ms_max, solves = reduce_over_ranks(float(np.sum(times)), conv, dev)
     value = solves / (ms_max / 1e3)
 
     # ---- end to end through the public API with host buffers; the FFT
