@@ -293,6 +293,17 @@ lsw_status lsw_autotune(const lsw_green* g, int prec, int nbatch, void* stream,
  * comparisons and reproducibility across paths. */
 lsw_status lsw_set_tensor_cores(int enable);
 
+/* Process-wide switch (default on) for CUDA graphs in the solvers: inside a
+ * flexible-GMRES call, the Arnoldi step's preconditioner apply and operator
+ * (fixed buffers) are captured once into a CUDA graph and replayed at every
+ * later step.  Results are the same either way (the same kernels in the
+ * same order); a capture that fails falls back to ordinary launches.  Not
+ * part of the method. */
+lsw_status lsw_set_graphs(int enable);
+/* Number of CUDA-graph launches the solvers have issued in this process
+ * (diagnostics). */
+uint64_t lsw_graph_replay_count(void);
+
 /* ------------------------------------------------------------------------
  * Learned right preconditioner.  The paper has no network: its Sec. 3.2
  * compares the preconditioned series with GMRES, and this is a Fourier

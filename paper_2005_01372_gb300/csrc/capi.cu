@@ -18,6 +18,18 @@ static thread_local char g_last_error[512];
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_counter() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+std::atomic<unsigned long long> g_replays{0};
+}
+void count_graph_replay() { g_replays.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+std::atomic<int> g_graphs{1};
+}
+bool graphs_enabled() { return g_graphs.load() != 0; }
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
     snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
@@ -48,6 +60,9 @@ void drain_timer() {
 KTimer::KTimer(const char* family, cudaStream_t st, double bytes, double flops) {
     std::lock_guard<std::mutex> lk(g_timer.mu);
     if (!g_timer.on || strncmp(family, g_timer.family, sizeof g_timer.family) != 0) return;
+    // work being captured into a graph does not run now: nothing to time
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     st_ = st;
     bytes_ = bytes;
     flops_ = flops;
@@ -131,6 +146,14 @@ static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 static bool grid_ok(int n) { return n >= 1 && n <= 2048 && is_pow2(n); }
 
 extern "C" {
+
+uint64_t lsw_graph_replay_count(void) { return lsw::g_replays.load(); }
+
+lsw_status lsw_set_graphs(int enable) {
+    lsw::g_graphs.store(enable != 0 ? 1 : 0);
+    return LSW_OK;
+}
+
 
 const char* lsw_status_string(lsw_status s) {
     switch (s) {

@@ -66,6 +66,13 @@ template <typename C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
 void count_launch();
+// Add n launches to the counter (the kernels of a CUDA graph replay; n < 0
+// takes back kernels that were captured but never ran).
+void count_launches(long long n);
+unsigned long long launch_counter();
+void count_graph_replay();
+// Process-wide switch (default on) for replaying captured CUDA graphs.
+bool graphs_enabled();
 
 // Diagnostic timing of one kernel family (lsw_kernel_timer_*): while the
 // family named at lsw_kernel_timer_start is enabled, a KTimer records CUDA

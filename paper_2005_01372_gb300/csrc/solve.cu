@@ -169,6 +169,80 @@ lsw_status series_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     return LSW_OK;
 }
 
+// ------------------------------------------------------------- step graph
+// The Arnoldi step's fixed-buffer work (v_j -> z_j = H v_j -> w = A z_j) as
+// one CUDA graph: the first run() eagerly runs it, the second captures it on
+// a stream of its own (the caller's may be the legacy default stream, which
+// cannot capture) and every run() from then on replays it there, ordered
+// after and before the caller's stream by two events: one launch instead of
+// a dozen.  Any capture or instantiation failure, a caller that is itself
+// capturing, or graphs switched off keeps the eager path.  Replays add the
+// captured kernels to the launch counter.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;                 // capture and replay stream (the
+    cudaEvent_t in = nullptr, out = nullptr;   // caller's may be the legacy one)
+    int runs = 0;
+    bool failed = false;
+    long long launches = 0;
+    ~StepGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (in) cudaEventDestroy(in);
+        if (out) cudaEventDestroy(out);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    // body(stream) enqueues the step on the given stream
+    template <typename F>
+    lsw_status run(cudaStream_t st, F&& body) {
+        ++runs;
+        if (exec) return replay(st);
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (failed || runs < 2 || !graphs_enabled() || cudaStreamIsCapturing(st, &cap) != cudaSuccess ||
+            cap != cudaStreamCaptureStatusNone)
+            return body(st);
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return body(st);
+        }
+        const unsigned long long l0 = launch_counter();
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return body(st);
+        }
+        const lsw_status s = body(cs);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &gr);
+        launches = (long long)(launch_counter() - l0);
+        if (s == LSW_OK && e == cudaSuccess && gr && cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) exec = nullptr;
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        if (!exec) {
+            // nothing captured ran: take back its count and run it eagerly
+            failed = true;
+            count_launches(-launches);
+            return body(st);
+        }
+        count_launches(-launches);              // counted again by the replay
+        return replay(st);
+    }
+
+  private:
+    lsw_status replay(cudaStream_t st) {
+        LSW_CUDA(cudaEventRecord(in, st));
+        LSW_CUDA(cudaStreamWaitEvent(cs, in, 0));
+        LSW_CUDA(cudaGraphLaunch(exec, cs));
+        LSW_CUDA(cudaEventRecord(out, cs));
+        LSW_CUDA(cudaStreamWaitEvent(st, out, 0));
+        count_launches(launches);
+        count_graph_replay();
+        return LSW_OK;
+    }
+};
+
 // ----------------------------------------------------------------- FGMRES
 // Flexible GMRES(m) for nb independent sources in lockstep, from x = 0, with
 // H (or the learned network while it is on) as right preconditioner; Arnoldi
@@ -216,6 +290,7 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
     const C one_ = mk((R)1, (R)0), zero_ = mk((R)0, (R)0), mone = mk((R)-1, (R)0);
     int total = 0;
     const size_t pitchV = sizeof(C) * n * (m + 1), pitchZ = sizeof(C) * n * m, row = sizeof(C) * n;
+    StepGraph sg;
     while (true) {
         // r = b - A x  (RESIDUAL gives x - G0V x - b = -r)
         LSW_TRY(op_full<R>(g, chi, LSW_OP_RESIDUAL, x, b, w.as<C>(), nb, work, st));
@@ -250,12 +325,17 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
         int j = 0;
         for (; j < m; ++j) {
             // z_j = H v_j (or the network's z_j) ; w = A z_j
-            if (learned)
+            if (learned) {
                 LSW_TRY(fno_apply_precond(lp->fno, g, chi, vj.p, zj.p, nb, sizeof(R) == 8 ? LSW_C128 : LSW_C64, st));
-            else if (h) LSW_TRY(apply_h<R>(h, vj.as<C>(), zj.as<C>(), nb, st));
-            else LSW_CUDA(cudaMemcpyAsync(zj.p, vj.p, sizeof(C) * n * nb, cudaMemcpyDeviceToDevice, st));
+                LSW_TRY(op_full<R>(g, chi, LSW_OP_RESIDUAL, zj.as<C>(), nullptr, w.as<C>(), nb, work, st));
+            } else {
+                LSW_TRY(sg.run(st, [&](cudaStream_t ss) -> lsw_status {
+                    if (h) LSW_TRY(apply_h<R>(h, vj.as<C>(), zj.as<C>(), nb, ss));
+                    else LSW_CUDA(cudaMemcpyAsync(zj.p, vj.p, sizeof(C) * n * nb, cudaMemcpyDeviceToDevice, ss));
+                    return op_full<R>(g, chi, LSW_OP_RESIDUAL, zj.as<C>(), nullptr, w.as<C>(), nb, work, ss);
+                }));
+            }
             LSW_CUDA(cudaMemcpy2DAsync(Zb.as<char>() + row * j, pitchZ, zj.p, row, row, nb, cudaMemcpyDeviceToDevice, st));
-            LSW_TRY(op_full<R>(g, chi, LSW_OP_RESIDUAL, zj.as<C>(), nullptr, w.as<C>(), nb, work, st));
             // two passes of classical Gram-Schmidt against v_0..v_j, then the
             // norm of what is left: the coefficients of both passes and the
             // norms come back to the host together, one wait per iteration

@@ -100,6 +100,8 @@ _SIGS = {
                                 ctypes.POINTER(SolveInfo), VP]),
     "lsw_autotune": (I32, [VP, I32, I32, VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "lsw_set_tensor_cores": (I32, [I32]),
+    "lsw_set_graphs": (I32, [I32]),
+    "lsw_graph_replay_count": (ctypes.c_uint64, []),
     "lsw_fno_create": (I32, [ctypes.POINTER(_FnoParams), VP, ctypes.POINTER(VP)]),
     "lsw_fno_destroy": (I32, [VP]),
     "lsw_fno_num_params": (I32, [VP, ctypes.POINTER(ctypes.c_int64)]),
@@ -261,6 +263,16 @@ def kernel_timer_stop():
 def set_tensor_cores(enable: bool):
     """Process-wide switch for the tensor-core products of H's dense leaves."""
     _check(lib().lsw_set_tensor_cores(1 if enable else 0), "lsw_set_tensor_cores")
+
+
+def set_graphs(enable: bool):
+    """Process-wide switch for the solvers' CUDA-graph replay of the Arnoldi step."""
+    _check(lib().lsw_set_graphs(1 if enable else 0), "lsw_set_graphs")
+
+
+def graph_replay_count() -> int:
+    """CUDA-graph launches the solvers have issued so far in this process."""
+    return int(lib().lsw_graph_replay_count())
 
 
 def build_green(nz, nx, h, c0, freq_hz, stream=None) -> Green:
