@@ -86,7 +86,11 @@ typedef struct {
     int32_t rank;         /* r, the same for every low-rank block (Sec. 2.4)  */
     int32_t oversample;   /* extra probes p: r + p Gaussian columns           */
     int32_t q;            /* power iterations of Algorithm 2 (0 on the paper's HODLR path) */
-    int32_t pad_;
+    int32_t rank_max;     /* lsw_solve_batched, HODLR: when > rank, a problem
+                             that leaves a source unconverged is rebuilt with
+                             twice the rank (at most rank_max and 64 -
+                             oversample) and solved again (Sec. 3.1: raise r
+                             and rebuild); 0 = fixed rank                      */
     uint64_t seed;        /* Philox4x32-10 key of every probe block           */
 } lsw_hparams;
 
@@ -269,8 +273,11 @@ typedef struct {
  * most 7) are worked on at once from host worker threads, each on its own
  * stream, so that their builds and solves overlap on the GPU.  The call
  * first synchronises `stream` (inputs may come from it) and returns when
- * every problem is done.  info: HOST array with one record per source, in
- * problem order.  Returns LSW_OK, or the first failing problem's status. */
+ * every problem is done.  With hp->rank_max > hp->rank (HODLR), a problem
+ * that leaves a source unconverged, diverging or non-finite is rebuilt with twice the
+ * rank, up to rank_max, and solved again.  info: HOST array with one record
+ * per source, in problem order (the last attempt's).  Returns LSW_OK, or the
+ * first failing problem's status. */
 lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hparams* hp,
                              const lsw_solve_params* sp, int max_concurrent,
                              lsw_solve_info* info, void* stream);

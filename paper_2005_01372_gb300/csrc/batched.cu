@@ -168,10 +168,24 @@ lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hpar
             if (st == LSW_OK && cudaMallocAsync(&u0, elem * n * p.nsrc, s) != cudaSuccess) st = LSW_ERR_OOM;
             if (st == LSW_OK) st = lsw_contrast(g, p.velocity, (double*)chi, s);
             if (st == LSW_OK) st = lsw_point_sources(g, p.sources, p.nsrc, upcast, u0, s);
-            if (st == LSW_OK && hp) st = lsw_build_hmatrix(g, (const double*)chi, hp, s, &h);
-            if (st == LSW_OK) {
-                const lsw_status r = lsw_solve_series(g, (const double*)chi, h, u0, p.u, p.nsrc, sp, info + offset[i], s);
-                st = r;
+            // rank adaptation: a problem that leaves a source unconverged is
+            // rebuilt with twice the rank (at most rank_max) and solved again
+            lsw_hparams hpl;
+            if (hp) hpl = *hp;
+            for (;;) {
+                if (st == LSW_OK && hp) st = lsw_build_hmatrix(g, (const double*)chi, &hpl, s, &h);
+                if (st != LSW_OK) break;
+                st = lsw_solve_series(g, (const double*)chi, h, u0, p.u, p.nsrc, sp, info + offset[i], s);
+                // the sketches take at most 64 probes: rank + oversample <= 64
+                const int next = hp ? std::min({hpl.rank_max, 2 * hpl.rank, 64 - hpl.oversample}) : 0;
+                const bool retry = hp && hpl.kind == LSW_H_HODLR && next > hpl.rank &&
+                                   (st == LSW_ERR_NOT_CONVERGED || st == LSW_ERR_DIVERGED ||
+                                    st == LSW_ERR_NUMERIC);
+                if (!retry) break;
+                lsw_destroy_hmatrix(h);
+                h = nullptr;
+                hpl.rank = next;
+                st = LSW_OK;
             }
             if (h) lsw_destroy_hmatrix(h);
             if (chi) cudaFreeAsync(chi, s);

@@ -45,7 +45,7 @@ class _Box(ctypes.Structure):
 class _HParams(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("rank", ctypes.c_int32), ("oversample", ctypes.c_int32),
-                ("q", ctypes.c_int32), ("pad_", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("q", ctypes.c_int32), ("rank_max", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class _SolveParams(ctypes.Structure):
@@ -171,10 +171,11 @@ class HParams:
     oversample: int = 10
     q: int = 0
     seed: int = 1
+    rank_max: int = 0
 
     def c(self):
-        return _HParams(self.kind, self.prec, self.levels, self.split, self.rank, self.oversample, self.q, 0,
-                        self.seed)
+        return _HParams(self.kind, self.prec, self.levels, self.split, self.rank, self.oversample, self.q,
+                        self.rank_max, self.seed)
 
 
 @dataclass

@@ -69,3 +69,26 @@ def test_batched_rejects_bad_problem(lsw):
         lsw.solve_batched([dict(nz=16, nx=16, h=10.0, c0=2000.0, freq_hz=5.0,
                                 velocity=torch.zeros(256, dtype=torch.float64, device="cuda"), sources=[])],
                           None, lsw.SolveParams(prec=lsw.C128))
+
+
+def test_batched_rank_adaptation_rebuilds_until_converged(lsw):
+    """The 256 x 256 salt medium at 15 Hz: with rank 20 the preconditioned
+    series diverges; allowed to raise the rank, the batched call rebuilds H
+    at rank 40 and converges, with the same result as a rank-40 solve."""
+    wl = media.layered_salt(256, 15.0, 32, 2)
+    vel = torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).cuda()
+    prob = dict(nz=256, nx=256, h=wl.h, c0=wl.c0, freq_hz=wl.freq_hz, velocity=vel, sources=list(wl.sources[:2]))
+    sp = lsw.SolveParams(prec=lsw.C64, method=lsw.SERIES, tol=1e-5, max_iter=40)
+    hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=6, rank=20, oversample=10, seed=1002)
+    _, inf0 = lsw.solve_batched([prob], hp, sp)
+    assert any(i.status != 0 for i in inf0[0])
+    hp.rank_max = 40
+    outs, inf1 = lsw.solve_batched([prob], hp, sp)
+    assert all(i.status == 0 for i in inf1[0]), [(i.status, i.rel_residual) for i in inf1[0]]
+    G = lsw.build_green(256, 256, wl.h, wl.c0, wl.freq_hz)
+    chi = G.contrast(vel)
+    H40 = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=6, rank=40, oversample=10,
+                                                seed=1002))
+    u, inf = lsw.solve_series(G, chi, H40, G.point_sources(prob["sources"], lsw.C64), sp=sp)
+    assert torch.equal(outs[0], u)
+    assert [i.iterations for i in inf] == [i.iterations for i in inf1[0]]

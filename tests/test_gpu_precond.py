@@ -281,3 +281,16 @@ def test_fgmres_graph_replay_matches_ordinary_launches(lsw, prec):
     assert i1 == i2
     assert torch.equal(u1, u2)
     assert n1 == n2
+
+
+def test_hodlr_power_iteration_parity_c128(lsw):
+    """Level sketches with one power iteration (Algorithm 2, q = 1) against
+    the oracle drawing the same probes."""
+    P, G, chi = _setup(lsw, 32, 32, seed=9, freq=20.0)
+    H = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C128, levels=3, rank=8, oversample=4, q=1,
+                                              seed=21))
+    ref = oh.HODLRPreconditioner(P, 3, 8, 4, 1, 21)
+    rng = np.random.default_rng(8)
+    x = media.complex_field(rng, (3, P.n))
+    y = lsw.apply_precond(H, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert _rel(y, ref.apply(x.T).T) < 1e-10
