@@ -274,7 +274,8 @@ def run_extra(args):
       32, 33) on 128^2, 256^2, 512^2 (h = 10 m) at 5, 10, ..., 40 Hz with 64
       sources each (1536 solves), solved through lsw_solve_batched (HODLR with
       32 x 32 leaves, rank 20 + 10, FP32; FP32 FGMRES(30) in FP64 refinement
-      to 1e-6), four problems at a time.
+      to 1e-6), four problems at a time; --rank-max R lets a problem that
+      does not converge be rebuilt with a doubled rank, up to R.
     c128-one-at-a-time: the headline 256^2 salt workload on the plain FP64
       path, one source per solve call: c128 operator, HODLR in FP64, FGMRES(30)
       in FP64; the build is charged once per 32 sources."""
@@ -292,7 +293,8 @@ def run_extra(args):
                 wl = media.layered_anomaly(n, f, 64, seed)
                 probs.append({"nz": n, "nx": n, "h": wl.h, "c0": wl.c0, "freq_hz": f, "sources": wl.sources,
                               "velocity": torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).to(dev)})
-            hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=levels, rank=20, oversample=10, seed=1002)
+            hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=levels, rank=20, oversample=10, seed=1002,
+                             rank_max=args.rank_max)
             groups.append((probs, hp))
         sp = lsw.SolveParams(prec=lsw.MIXED, method=lsw.FGMRES, tol=TOL, inner_tol=1e-3, restart=30, max_iter=120,
                              max_outer=8)
@@ -308,7 +310,9 @@ def run_extra(args):
                     per.append(good)
             return ok, total, per
         cfg = {"workload": "layered-anomaly-{128,256,512}^2-5..40Hz-64src-batched", "problems": 24,
-               "sources_per_problem": 64, "preconditioner": "HODLR 32x32 leaves, rank 20+10, FP32",
+               "sources_per_problem": 64,
+               "preconditioner": f"HODLR 32x32 leaves, rank 20+10, FP32, rank raised up to {args.rank_max}"
+               if args.rank_max > 20 else "HODLR 32x32 leaves, rank 20+10, FP32",
                "solver": "FGMRES(30) in FP64 refinement to 1e-6, lsw_solve_batched, 4 concurrent"}
     else:
         wl = media.layered_salt(256, 15.0, 32, 2)
@@ -434,6 +438,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "anomaly-batched", "c128-one-at-a-time"],
                     help="the headline workload (default) or a further measured one")
+    ap.add_argument("--rank-max", type=int, default=0, help="anomaly-batched: rank adaptation limit (0: off)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
