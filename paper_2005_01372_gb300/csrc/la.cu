@@ -1508,7 +1508,10 @@ lsw_status qr_explicit(typename Cx<R>::T* A, int m, int k, long long sA, int bat
         attr[sizeof(R) == 8] = true;
     }
     const long long nchL = (m + cmaxL - 1) / cmaxL;
-    const bool small = cmaxS >= 2 * k && (m <= cmaxS || nchL * batch < 3LL * 152);
+    // one large chunk per block (no second TSQR level) wins when the blocks
+    // fit and there are no more of them than SMs
+    const bool one_large = nchL == 1 && batch <= 152;
+    const bool small = cmaxS >= 2 * k && (m <= cmaxS || (!one_large && nchL * batch < 3LL * 152));
     const int cmax = small ? cmaxS : cmaxL;
     // Tall-skinny QR (TSQR): factor row chunks independently, then the
     // stacked R factors, then combine.  Every chunk has >= cmax/2 >= k rows.
