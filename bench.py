@@ -207,11 +207,9 @@ def run_ours(args):
     ms_max, solves = reduce_over_ranks(float(np.sum(times)), conv, dev)
     value = solves / (ms_max / 1e3)
 
-    # ---- end to end through the public API with host buffers; the FFT
-    # operator's three passes are timed live inside these solves
+    # ---- end to end through the public API with host buffers
     e2e_times = []
     out_host = torch.empty((len(wl.sources), wl.n), dtype=torch.complex128).pin_memory()
-    lsw.kernel_timer_start("operator_c64")
     for _ in range(max(1, min(args.steps, 2))):
         flush.zero_()
         torch.cuda.synchronize()
@@ -223,10 +221,25 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
-    op_ms, op_bytes, op_flops, op_n = lsw.kernel_timer_read()
-    lsw.kernel_timer_stop()
     e2e_value = sum(1 for i in infos if i.status == 0 and i.rel_residual <= TOL) * world / (
         float(np.mean(e2e_times)) / 1e3)
+
+    # ---- the FFT operator alone (its three passes timed with CUDA events on
+    # its stream): the step's RESIDUAL apply in FP32 on the 32 source fields,
+    # with L2 flushed between applies (inside the solves most operator applies
+    # are replayed from a CUDA graph, which the family timer does not see)
+    G = lsw.build_green(wl.nz, wl.nx, wl.h, wl.c0, wl.freq_hz)
+    chi = G.contrast(vel)
+    uf = G.point_sources(wl.sources, lsw.C64)
+    yf = torch.empty_like(uf)
+    lsw.apply_operator(G, chi, uf, uf, lsw.OP_RESIDUAL, y=yf)
+    torch.cuda.synchronize()
+    lsw.kernel_timer_start("operator_c64")
+    for _ in range(20):
+        flush.zero_()
+        lsw.apply_operator(G, chi, uf, uf, lsw.OP_RESIDUAL, y=yf)
+    op_ms, op_bytes, op_flops, op_n = lsw.kernel_timer_read()
+    lsw.kernel_timer_stop()
 
     peak, peak_kind = load_peaks()
     fp32_peak = fp32_alu_peak_tflops()
@@ -238,7 +251,8 @@ def run_ours(args):
             "achieved_tflops": round(dom_flops / (dom_ms / 1e3) / 1e12, 3) if dom_ms > 0 else 0.0}
     op_tf = op_flops / (op_ms / 1e3) / 1e12 if op_ms > 0 else 0.0
     op_gbs = op_bytes / (op_ms / 1e3) / 1e9 if op_ms > 0 else 0.0
-    op_roof = {"kernel": "FFT operator in FP32, passes k_fa + k_fb + k_fc, timed inside the solves", "bound": "alu",
+    op_roof = {"kernel": "FFT operator in FP32, passes k_fa + k_fb + k_fc, RESIDUAL on the 32 source fields, "
+                         "timed alone with L2 flushed between applies", "bound": "alu",
                "achieved": round(op_tf, 2), "peak": fp32_peak,
                "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                "unit": "TFLOP/s", "frac": round(op_tf / fp32_peak, 4), "algorithmic_gbs": round(op_gbs, 1),
