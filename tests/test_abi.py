@@ -65,3 +65,31 @@ def test_invalid_arguments_fail_without_touching_the_gpu(libpath):
     assert lib.lsw_build_green(None, None, None) == 1          # LSW_ERR_INVALID_ARG
     lib.lsw_apply_operator.restype = ctypes.c_int
     assert lib.lsw_apply_operator(None, 0, None, None, None, None, 1, 0, None) == 1
+
+
+def _header_struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in lsw.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "int32_t nz, nx" / "double h" / "const double* velocity" / "lsw_grid grid"
+        head, *rest = decl.split(",")
+        names = [head.split()[-1]] + [r.strip() for r in rest]
+        fields += [n.lstrip("*") for n in names]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("lsw_grid", "_Grid"), ("lsw_box", "_Box"), ("lsw_hparams", "_HParams"),
+                                          ("lsw_solve_params", "_SolveParams"), ("lsw_solve_info", "SolveInfo"),
+                                          ("lsw_problem", "_Problem"), ("lsw_fno_params", "_FnoParams")])
+def test_binding_struct_fields_follow_the_header(cname, pyname):
+    from paper_2005_01372_gb300 import lsw
+    want = _header_struct_fields(cname)
+    got = [f[0] for f in getattr(lsw, pyname)._fields_]
+    assert got == want, (cname, got, want)
