@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(256)
 k_gram_partial(const C* __restrict__ Y, int m, int k, long long sY, int nchunk, double2* __restrict__ part) {
     constexpr int TR = 32, MAXQ = 16;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    C* sy = reinterpret_cast<C*>(sm_raw);      // TR rows x k
+    C* sy = reinterpret_cast<C*>(sm_raw);      // k columns of TR rows, stride TR + 1 (odd: lanes on
+                                               // different columns hit different banks)
     const int b = blockIdx.y, ch = blockIdx.x;
     const int rows_per = (m + nchunk - 1) / nchunk;
     const int r0 = ch * rows_per, r1 = min(m, r0 + rows_per);
@@ -323,7 +324,7 @@ k_gram_partial(const C* __restrict__ Y, int m, int k, long long sY, int nchunk, 
         const int nr = min(TR, r1 - rr);
         for (int e = threadIdx.x; e < TR * k; e += 256) {
             const int c = e / TR, r = e % TR;
-            sy[c * TR + r] = r < nr ? Yb[(long long)c * m + rr + r] : czero<C>();
+            sy[c * (TR + 1) + r] = r < nr ? Yb[(long long)c * m + rr + r] : czero<C>();
         }
         __syncthreads();
 #pragma unroll
@@ -331,8 +332,8 @@ k_gram_partial(const C* __restrict__ Y, int m, int k, long long sY, int nchunk, 
             const int pidx = threadIdx.x + q * 256;
             if (pidx < npair) {
                 const int i = pidx % k, j = pidx / k;
-                const C* yi = sy + i * TR;
-                const C* yj = sy + j * TR;
+                const C* yi = sy + i * (TR + 1);
+                const C* yj = sy + j * (TR + 1);
                 // products and the sum over one tile in the data's precision,
                 // tiles accumulated in FP64
                 typedef decltype(yi->x) R;
@@ -660,9 +661,13 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int m = (k + 1) & ~1;                 // even number of players
     C* A = reinterpret_cast<C*>(sm_raw);        // k x k, column-major
-    C* V = A + k * k;
-    R* rot = reinterpret_cast<R*>(V + k * k);   // per pair: cs, sn, cos(phi), sin(phi)
+    C* A2 = A + k * k;                          // the next round's A
+    C* V = A2 + k * k;
+    C* us = V + k * k;                          // per index a: U(a, a)
+    C* up = us + k;                             // per index a: U(a', a), a' its partner
+    R* rot = reinterpret_cast<R*>(up + k);      // per pair: cs, sn, cos(phi), sin(phi)
     int2* pr = reinterpret_cast<int2*>(rot + 4 * (m / 2));
+    int* partner = reinterpret_cast<int*>(pr + m / 2);
     __shared__ C red[33];
     __shared__ double trs;
     __shared__ int order[64];
@@ -719,38 +724,47 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 }
                 rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
                 pr[i] = make_int2(p, q);
+                // U on (p, q): col p of U = cs e_p - sn e^{-i phi} e_q,
+                //              col q of U = sn e_p + cs e^{-i phi} e_q
+                const C em = mk(cp, -spp);
+                if (q < k) {
+                    us[p] = mk(cs, (R)0);
+                    up[p] = mk(-sn * em.x, -sn * em.y);
+                    partner[p] = q;
+                    us[q] = mk(cs * em.x, cs * em.y);
+                    up[q] = mk(sn, (R)0);
+                    partner[q] = p;
+                } else if (p < k) {
+                    us[p] = mk((R)1, (R)0);
+                    up[p] = czero<C>();
+                    partner[p] = p;
+                }
             }
             __syncthreads();
-            // columns: A <- A U, V <- V U with U on (p, q):
-            //   col p' = cs col p - sn e^{-i phi} col q ;  col q' = sn col p + cs e^{-i phi} col q
+            // A <- U^H A U in one pass from the old A into the other buffer:
+            //   A'(a, b) = conj(U(a,a)) [A(a,b) U(b,b) + A(a,b') U(b',b)]
+            //            + conj(U(a',a)) [A(a',b) U(b,b) + A(a',b') U(b',b)]
+            // and V <- V U in place, a pair of columns per item
+            for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+                const int b = e / k, a = e - b * k;
+                const int a2 = partner[a], b2 = partner[b];
+                const C ub = us[b], ub2 = up[b];
+                const C top = cadd(cmul(A[b * k + a], ub), cmul(A[b2 * k + a], ub2));
+                const C bot = cadd(cmul(A[b * k + a2], ub), cmul(A[b2 * k + a2], ub2));
+                A2[e] = cadd(cmulc(us[a], top), cmulc(up[a], bot));
+            }
             for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
                 const int i = e / k, row = e - i * k;
                 const int p = pr[i].x, q = pr[i].y;
                 if (q >= k) continue;
                 const R cs = rot[4 * i], sn = rot[4 * i + 1];
                 const C em = mk(rot[4 * i + 2], -rot[4 * i + 3]);   // e^{-i phi}
-                for (int w = 0; w < 2; ++w) {
-                    C* M = w ? V : A;
-                    const C ap = M[p * k + row], aq = M[q * k + row];
-                    const C eq = cmul(em, aq);
-                    M[p * k + row] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
-                    M[q * k + row] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
-                }
+                const C vp = V[p * k + row], eq = cmul(em, V[q * k + row]);
+                V[p * k + row] = mk(cs * vp.x - sn * eq.x, cs * vp.y - sn * eq.y);
+                V[q * k + row] = mk(sn * vp.x + cs * eq.x, sn * vp.y + cs * eq.y);
             }
             __syncthreads();
-            // rows: A <- U^H A:  row p' = cs row p - sn e^{i phi} row q ; row q' = sn row p + cs e^{i phi} row q
-            for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
-                const int i = e / k, col = e - i * k;
-                const int p = pr[i].x, q = pr[i].y;
-                if (q >= k) continue;
-                const R cs = rot[4 * i], sn = rot[4 * i + 1];
-                const C ep = mk(rot[4 * i + 2], rot[4 * i + 3]);
-                const C ap = A[col * k + p], aq = A[col * k + q];
-                const C eq = cmul(ep, aq);
-                A[col * k + p] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
-                A[col * k + q] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
-            }
-            __syncthreads();
+            { C* t = A; A = A2; A2 = t; }
         }
         if (nrot == 0) break;          // a sweep without a rotation: converged
         __syncthreads();
@@ -1557,7 +1571,7 @@ lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int ba
     const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
     DevBuf part;
     LSW_TRY(part.alloc(sizeof(double2) * (size_t)batch * nchunk * k * k, st));
-    k_gram_partial<CT><<<dim3(nchunk, batch), 256, sizeof(CT) * 32 * k, st>>>(Y, m, k, sY, nchunk,
+    k_gram_partial<CT><<<dim3(nchunk, batch), 256, sizeof(CT) * 33 * k, st>>>(Y, m, k, sY, nchunk,
                                                                                 part.as<double2>());
     LSW_LAUNCH_CHECK();
     k_gram_reduce<<<grid_for((long long)batch * k * k), 256, 0, st>>>(part.as<double2>(), nchunk, k * k, batch, G);
@@ -1587,10 +1601,11 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
     }
     static std::atomic<bool> attrb[2];
     if (!attrb[sizeof(R) == 8]) {
-        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
         attrb[sizeof(R) == 8] = true;
     }
-    const size_t smb = sizeof(CT) * 2 * k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2);
+    const size_t smb = sizeof(CT) * (3 * (size_t)k * k + 2 * (size_t)k) + sizeof(R) * 4 * (m / 2) +
+                       sizeof(int2) * (m / 2) + sizeof(int) * (size_t)k;
     k_heev_jacobi<R><<<batch, 256, smb, st>>>(G, V, k);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
