@@ -52,7 +52,10 @@ enum {
     LSW_ERR_TIMEOUT = 8           /* reserved for bounded device-side waits  */
 };
 
-typedef enum { LSW_C128 = 0, LSW_C64 = 1, LSW_MIXED = 2 } lsw_prec;
+/* LSW_BF16 is for H only (lsw_hparams.prec, HODLR): built in FP32, then kept
+ * as BF16 (re, im) pairs, half the memory of LSW_C64, and applied to complex64
+ * vectors with FP32 accumulation; a solve treats such an H as LSW_C64. */
+typedef enum { LSW_C128 = 0, LSW_C64 = 1, LSW_MIXED = 2, LSW_BF16 = 3 } lsw_prec;
 
 /* Products computed by lsw_apply_operator (Eq. 4, Eq. 13, Algorithm 2). */
 typedef enum {
@@ -80,7 +83,8 @@ typedef enum { LSW_SPLIT_QUADTREE = 0, LSW_SPLIT_STRIPS = 1 } lsw_split;
 
 typedef struct {
     int32_t kind;         /* lsw_h_kind                                       */
-    int32_t prec;         /* LSW_C128 or LSW_C64: storage and arithmetic of H */
+    int32_t prec;         /* LSW_C128 or LSW_C64: storage and arithmetic of H;
+                             LSW_BF16 (HODLR): FP32 build, BF16 storage     */
     int32_t levels;       /* HODLR: levels of the cluster tree (leaves at L)  */
     int32_t split;        /* HODLR: lsw_split                                 */
     int32_t rank;         /* r, the same for every low-rank block (Sec. 2.4)  */

@@ -11,6 +11,7 @@
 // the 2^L dense leaves are D[c], n_L x n_L.  The blocks inside node (l, c)
 // are therefore contiguous ranges of every deeper level's arrays, which turns
 // each operation on a subtree into a few strided batched products.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -128,6 +129,24 @@ template <typename R> struct LeafUpd {
     std::vector<int> end;
 };
 
+// H kept as BF16 pairs (re, im in one 32-bit word) after an FP32 build;
+// only the whole-matrix product runs on this storage.
+struct HStoreB {
+    int L = 0, r = 0, n = 0;
+    uint32_t* D = nullptr;
+    std::vector<uint32_t*> U, W;
+    size_t bytes = 0;
+    int nl(int l) const { return n >> l; }
+    void release() {
+        if (D) cudaFree(D);
+        for (auto p : U) if (p) cudaFree(p);
+        for (auto p : W) if (p) cudaFree(p);
+        D = nullptr;
+        U.clear();
+        W.clear();
+    }
+};
+
 }  // namespace lsw
 
 struct lsw_hmatrix {
@@ -136,6 +155,8 @@ struct lsw_hmatrix {
     int* perm_d = nullptr;
     lsw::HStore<float> h32;
     lsw::HStore<double> h64;
+    lsw::HStoreB hb;         // BF16 storage (bf16 true): h32 is released
+    bool bf16 = false;
     void* smwU = nullptr;    // n x r
     void* smwW = nullptr;    // n x r
     void* smwZ = nullptr;    // r x r
@@ -440,9 +461,16 @@ lsw_status build_level(const lsw_green* g, const double* chi, const Tree& tr, in
 // one pass over Y adding every level's G T.
 constexpr int kMaxLev = 16;
 
-template <typename C> struct LrLevels {
-    const C* F[kMaxLev];
-    const C* G[kMaxLev];
+// factor entries as stored (complex FP32 / FP64, or a BF16 pair in 32 bits)
+__device__ __forceinline__ float2 ldfac(const float2* p) { return *p; }
+__device__ __forceinline__ double2 ldfac(const double2* p) { return *p; }
+__device__ __forceinline__ float2 ldfac(const uint32_t* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+
+template <typename C, typename FT = C> struct LrLevels {
+    const FT* F[kMaxLev];
+    const FT* G[kMaxLev];
     int nb[kMaxLev];
     int ch[kMaxLev];                // rows per chunk (divides nb)
     int chunk0[kMaxLev + 1];        // first chunk of each level
@@ -455,9 +483,9 @@ template <typename C> struct LrLevels {
 // thread reads 2 x 2 complex at a time; thread (microtile, row group) keeps a
 // 4 x 4 block of outputs over every G-th row of the tile, and the row groups
 // are summed in shared memory at the end.
-template <typename C>
+template <typename C, typename FT>
 __global__ void __launch_bounds__(256)
-k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int swapA, C* __restrict__ P) {
+k_lr_partial(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ X, int swapA, C* __restrict__ P) {
     constexpr int TR = 32;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int rs = (r + 3) & ~3, ks = (k + 3) & ~3;       // columns rounded up to 4
@@ -472,7 +500,7 @@ k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int s
     const int row0 = chn * CH;
     const int j = row0 / nb, o = row0 - j * nb;
     const int src = swapA ? (j ^ 1) : j;
-    const C* Fj = lv.F[q] + (long long)j * nb * r + o;
+    const FT* Fj = lv.F[q] + (long long)j * nb * r + o;
     const C* Xg = X + (long long)src * nb + o;
     const int mtr = rs / 4, mtk = ks / 4, nmt = mtr * mtk;
     const int G = max(1, 256 / nmt);
@@ -488,7 +516,7 @@ k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int s
         const int nr = min(TR, CH - r0);
         for (int e = threadIdx.x; e < TR * rs; e += 256) {
             const int cc = e / TR, rr = e - cc * TR;
-            Fs[rr * fsd + cc] = (rr < nr && cc < r) ? Fj[(long long)cc * nb + r0 + rr] : czero<C>();
+            Fs[rr * fsd + cc] = (rr < nr && cc < r) ? ldfac(Fj + (long long)cc * nb + r0 + rr) : czero<C>();
         }
         for (int e = threadIdx.x; e < TR * ks; e += 256) {
             const int cc = e / TR, rr = e - cc * TR;
@@ -528,8 +556,8 @@ k_lr_partial(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ X, int s
 }
 
 // T[level q][block j] = sum over the block's chunks of the partials, in order.
-template <typename C>
-__global__ void k_lr_reduce(LrLevels<C> lv, int r, int k, const C* __restrict__ P, C* __restrict__ T) {
+template <typename C, typename FT>
+__global__ void k_lr_reduce(LrLevels<C, FT> lv, int r, int k, const C* __restrict__ P, C* __restrict__ T) {
     const long long nout = (long long)r * k;
     const long long tot = lv.t0[lv.nlev] * nout;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
@@ -549,9 +577,9 @@ __global__ void k_lr_reduce(LrLevels<C> lv, int r, int k, const C* __restrict__ 
 // Y[i][c] += sum over levels of G_b'(row) T_b': thread (4 consecutive rows,
 // group of 8 columns); the 4 rows share their block at every level (block
 // sizes are multiples of 4), so each T entry loaded serves 4 rows.
-template <typename C>
+template <typename C, typename FT>
 __global__ void __launch_bounds__(128)
-k_lr_apply(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ T, int swapC, C* __restrict__ Y) {
+k_lr_apply(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ T, int swapC, C* __restrict__ Y) {
     const int ngrp = (k + 7) / 8;
     const int slots = 128 / ngrp;
     const int slot = threadIdx.x % slots, g = threadIdx.x / slots;
@@ -569,12 +597,12 @@ k_lr_apply(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ T, int swa
         const int nb = lv.nb[q];
         const int b = i0 / nb, o = i0 - b * nb;
         const int bb = swapC ? (b ^ 1) : b;
-        const C* Gb = lv.G[q] + (long long)bb * nb * r + o;
+        const FT* Gb = lv.G[q] + (long long)bb * nb * r + o;
         const C* Tb = T + (lv.t0[q] + bb) * nout;
         for (int t = 0; t < r; ++t) {
             C gv[4], tv[8];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) gv[a] = Gb[(long long)t * nb + a];
+            for (int a = 0; a < 4; ++a) gv[a] = ldfac(Gb + (long long)t * nb + a);
 #pragma unroll
             for (int u = 0; u < 8; ++u) tv[u] = c0 + u < k ? Tb[(long long)(c0 + u) * r + t] : czero<C>();
 #pragma unroll
@@ -594,6 +622,32 @@ k_lr_apply(LrLevels<C> lv, int m, int r, int k, const C* __restrict__ T, int swa
         }
 }
 
+// The three launches of the fused level products for a prepared level list.
+template <typename C, typename FT>
+lsw_status lr_launch(const LrLevels<C, FT>& lv, int m, int r, int k, const C* X, C* Y, int swapA, int swapC,
+                     cudaStream_t st) {
+    const long long nout = (long long)r * k;
+    DevBuf P, T;
+    LSW_TRY(P.alloc(sizeof(C) * (size_t)lv.chunk0[lv.nlev] * nout, st));
+    LSW_TRY(T.alloc(sizeof(C) * (size_t)lv.t0[lv.nlev] * nout, st));
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        LSW_CUDA(cudaFuncSetAttribute(k_lr_partial<C, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr.store(true);
+    }
+    const int rs = (r + 3) & ~3, ks = (k + 3) & ~3;
+    const int Gr = std::max(1, 256 / ((rs / 4) * (ks / 4)));
+    const size_t smem = sizeof(C) * (32 * (size_t)(rs + ks + 2) + (size_t)Gr * r * k);
+    k_lr_partial<C, FT><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
+    LSW_LAUNCH_CHECK();
+    k_lr_reduce<C, FT><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
+    LSW_LAUNCH_CHECK();
+    const int rows_cta = 4 * (128 / ((k + 7) / 8));
+    k_lr_apply<C, FT><<<(m + rows_cta - 1) / rows_cta, 128, 0, st>>>(lv, m, r, k, T.as<C>(), swapC, Y);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
 // Shapes the fused kernels take: k <= 64 columns, rank <= 64, r k <= 4096,
 // block sizes (hence node sizes) multiples of 4.
 template <typename R>
@@ -610,7 +664,7 @@ lsw_status lr_levels(const HStore<R>& H, int l, int c, bool F_is_W, const typena
     if (L - l > kMaxLev) return LSW_ERR_UNSUPPORTED_SIZE;
     if (L <= l) return LSW_OK;
     if (r * k > 4096 || k > 64 || r > 64 || (m & 3)) return LSW_ERR_INVALID_ARG;
-    LrLevels<C> lv;
+    LrLevels<C, C> lv;
     lv.nlev = L - l;
     lv.chunk0[0] = 0;
     lv.t0[0] = 0;
@@ -632,26 +686,7 @@ lsw_status lr_levels(const HStore<R>& H, int l, int c, bool F_is_W, const typena
         lv.chunk0[q + 1] = lv.chunk0[q];
         lv.t0[q + 1] = lv.t0[q];
     }
-    const long long nout = (long long)r * k;
-    DevBuf P, T;
-    LSW_TRY(P.alloc(sizeof(C) * (size_t)lv.chunk0[lv.nlev] * nout, st));
-    LSW_TRY(T.alloc(sizeof(C) * (size_t)lv.t0[lv.nlev] * nout, st));
-    static std::atomic<bool> attr[2];
-    if (!attr[sizeof(R) == 8]) {
-        LSW_CUDA(cudaFuncSetAttribute(k_lr_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr[sizeof(R) == 8] = true;
-    }
-    const int rs = (r + 3) & ~3, ks = (k + 3) & ~3;
-    const int Gr = std::max(1, 256 / ((rs / 4) * (ks / 4)));
-    const size_t smem = sizeof(C) * (32 * (size_t)(rs + ks + 2) + (size_t)Gr * r * k);
-    k_lr_partial<C><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
-    LSW_LAUNCH_CHECK();
-    k_lr_reduce<C><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
-    LSW_LAUNCH_CHECK();
-    const int rows_cta = 4 * (128 / ((k + 7) / 8));
-    k_lr_apply<C><<<(m + rows_cta - 1) / rows_cta, 128, 0, st>>>(lv, m, r, k, T.as<C>(), swapC, Y);
-    LSW_LAUNCH_CHECK();
-    return LSW_OK;
+    return lr_launch<C, C>(lv, m, r, k, X, Y, swapA, swapC, st);
 }
 
 // Y_b = D_b X_b for nleaf consecutive dense leaves (nL x nL each) and k
@@ -1054,6 +1089,102 @@ lsw_status build_smw(const lsw_green* g, const double* chi, const lsw_hparams* h
     return LSW_OK;
 }
 
+__global__ void k_to_bf16(const float2* __restrict__ src, uint32_t* __restrict__ dst, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(src[e].x, src[e].y);
+        dst[e] = *reinterpret_cast<const uint32_t*>(&v);
+    }
+}
+
+// Y_b = D_b X_b with BF16 leaves on the CUDA cores (when the tensor-core
+// kernel does not take the shape or is switched off): thread per output.
+__global__ void k_leaf_bf16(const uint32_t* __restrict__ D, const float2* __restrict__ X, float2* __restrict__ Y,
+                            int nL, int nleaf, int k, int ld) {
+    const long long tot = (long long)nL * nleaf * k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % nL);
+        const long long rest = e / nL;
+        const int b = (int)(rest % nleaf), j = (int)(rest / nleaf);
+        const uint32_t* Db = D + (size_t)b * nL * nL;
+        const float2* x = X + (size_t)j * ld + (size_t)b * nL;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int t = 0; t < nL; ++t) cfma(acc, ldfac(Db + (size_t)t * nL + i), x[t]);
+        Y[(size_t)j * ld + (size_t)b * nL + i] = acc;
+    }
+}
+
+lsw_status to_bf16(const HStore<float>& H, HStoreB& B, cudaStream_t st) {
+    // the product on this storage runs on the fused level kernels only
+    if (H.L > kMaxLev || H.r > 64 || (H.L >= 1 && (H.nl(H.L) & 3))) return LSW_ERR_UNSUPPORTED_SIZE;
+    B.L = H.L;
+    B.r = H.r;
+    B.n = H.n;
+    const int nL = H.nl(H.L);
+    const long long nd = (long long)H.n * nL, nf = (long long)H.n * H.r;
+    if (cudaMalloc(&B.D, sizeof(uint32_t) * nd) != cudaSuccess) return LSW_ERR_OOM;
+    B.bytes = sizeof(uint32_t) * nd;
+    k_to_bf16<<<gridn(nd), 256, 0, st>>>(H.D, B.D, nd);
+    LSW_LAUNCH_CHECK();
+    B.U.assign(H.L + 1, nullptr);
+    B.W.assign(H.L + 1, nullptr);
+    for (int l = 1; l <= H.L; ++l) {
+        if (cudaMalloc(&B.U[l], sizeof(uint32_t) * nf) != cudaSuccess ||
+            cudaMalloc(&B.W[l], sizeof(uint32_t) * nf) != cudaSuccess)
+            return LSW_ERR_OOM;
+        B.bytes += 2 * sizeof(uint32_t) * nf;
+        k_to_bf16<<<gridn(nf), 256, 0, st>>>(H.U[l], B.U[l], nf);
+        LSW_LAUNCH_CHECK();
+        k_to_bf16<<<gridn(nf), 256, 0, st>>>(H.W[l], B.W[l], nf);
+        LSW_LAUNCH_CHECK();
+    }
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+// Y = H X for the whole matrix on BF16 storage (tree order, k columns, ld n)
+lsw_status hmv_bf16(const HStoreB& B, const float2* X, int k, float2* Y, cudaStream_t st) {
+    const int n = B.n, L = B.L, r = B.r, nL = B.nl(L), nleaf = 1 << L;
+    for (int c0 = 0; c0 < k; c0 += 32) {
+        const int kc = std::min(32, k - c0);
+        if (tc_gemm_enabled() && tc_bf16_fits(nL, kc, nL)) {
+            LSW_TRY(cgemm_tc_bf16(B.D, nL, (long long)nL * nL, X + (size_t)c0 * n, n, nL, Y + (size_t)c0 * n, n, nL, nL,
+                                  kc, nL, make_float2(1.f, 0.f), nleaf, st));
+        } else {
+            k_leaf_bf16<<<gridn((long long)n * kc), 256, 0, st>>>(B.D, X + (size_t)c0 * n, Y + (size_t)c0 * n, nL,
+                                                                 nleaf, kc, n);
+            LSW_LAUNCH_CHECK();
+        }
+    }
+    if (L < 1) return LSW_OK;
+    if ((nL & 3) || L > kMaxLev || r > 64) return LSW_ERR_UNSUPPORTED_SIZE;
+    // every level's U (W^H x[sibling]) in column blocks the fused kernels take
+    const int kb = std::max(1, std::min(64, 4096 / r));
+    for (int c0 = 0; c0 < k; c0 += kb) {
+        const int kc = std::min(kb, k - c0);
+        LrLevels<float2, uint32_t> lv;
+        lv.nlev = L;
+        lv.chunk0[0] = 0;
+        lv.t0[0] = 0;
+        for (int q = 0; q < L; ++q) {
+            const int lp = 1 + q, cnt = 1 << lp, nb = B.nl(lp);
+            lv.F[q] = B.W[lp];
+            lv.G[q] = B.U[lp];
+            lv.nb[q] = nb;
+            lv.ch[q] = std::min(nb, 256);
+            lv.chunk0[q + 1] = lv.chunk0[q] + n / lv.ch[q];
+            lv.t0[q + 1] = lv.t0[q] + cnt;
+        }
+        for (int q = L; q < kMaxLev; ++q) {
+            lv.F[q] = lv.G[q] = nullptr;
+            lv.nb[q] = lv.ch[q] = 1;
+            lv.chunk0[q + 1] = lv.chunk0[q];
+            lv.t0[q + 1] = lv.t0[q];
+        }
+        LSW_TRY((lr_launch<float2, uint32_t>(lv, n, r, kc, X + (size_t)c0 * n, Y + (size_t)c0 * n, 1, 0, st)));
+    }
+    return LSW_OK;
+}
+
 // y = H x (grid order, nb fields)
 template <typename R>
 lsw_status apply_h(const lsw_hmatrix* h, const typename Cx<R>::T* x, typename Cx<R>::T* y, int nb, cudaStream_t st) {
@@ -1072,6 +1203,17 @@ lsw_status apply_h(const lsw_hmatrix* h, const typename Cx<R>::T* x, typename Cx
         LSW_TRY(gemm<R>('N', 'N', r, nb, r, one<C>(), Z, r, 0, t1.as<C>(), r, 0, zero<C>(), t2.as<C>(), r, 0, 1, st));
         LSW_CUDA(cudaMemcpyAsync(y, x, sizeof(C) * (size_t)n * nb, cudaMemcpyDeviceToDevice, st));
         LSW_TRY(gemm<R>('N', 'N', n, nb, r, one<C>(), U, n, 0, t2.as<C>(), r, 0, one<C>(), y, n, 0, 1, st));
+        return LSW_OK;
+    }
+    if (sizeof(R) == 4 && h->bf16) {
+        DevBuf xt, yt;
+        LSW_TRY(xt.alloc(sizeof(C) * (size_t)n * nb, st));
+        LSW_TRY(yt.alloc(sizeof(C) * (size_t)n * nb, st));
+        k_permute<C><<<gridn((long long)n * nb), 256, 0, st>>>(x, xt.as<C>(), h->perm_d, n, nb, 0);
+        LSW_LAUNCH_CHECK();
+        LSW_TRY(hmv_bf16(h->hb, reinterpret_cast<const float2*>(xt.p), nb, reinterpret_cast<float2*>(yt.p), st));
+        k_permute<C><<<gridn((long long)n * nb), 256, 0, st>>>(yt.as<C>(), y, h->perm_d, n, nb, 1);
+        LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
     const HStore<R>& H = *reinterpret_cast<const HStore<R>*>(sizeof(R) == 8 ? (const void*)&h->h64 : (const void*)&h->h32);
@@ -1121,14 +1263,15 @@ lsw_status lsw_build_hmatrix(const lsw_green* g, const double* chi, const lsw_hp
                              lsw_hmatrix** out) {
     if (!g || !chi || !hp || !out) return LSW_ERR_INVALID_ARG;
     *out = nullptr;
-    if (hp->prec != LSW_C128 && hp->prec != LSW_C64) return LSW_ERR_INVALID_ARG;
+    if (hp->prec != LSW_C128 && hp->prec != LSW_C64 && !(hp->prec == LSW_BF16 && hp->kind == LSW_H_HODLR))
+        return LSW_ERR_INVALID_ARG;
     if (hp->rank <= 0 || hp->oversample < 0 || hp->q < 0 || hp->rank + hp->oversample > 64) return LSW_ERR_INVALID_ARG;
     if (hp->kind != LSW_H_LOWRANK_SMW && hp->kind != LSW_H_HODLR) return LSW_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     lsw_hmatrix* h = new (std::nothrow) lsw_hmatrix();
     if (!h) return LSW_ERR_OOM;
     h->kind = hp->kind;
-    h->prec = hp->prec;
+    h->prec = hp->prec == LSW_BF16 ? LSW_C64 : hp->prec;     // vectors are complex64 for BF16 storage
     h->n = g->nz * g->nx;
     h->nz = g->nz;
     h->nx = g->nx;
@@ -1155,6 +1298,14 @@ lsw_status lsw_build_hmatrix(const lsw_green* g, const double* chi, const lsw_hp
             } else {
                 s = build_hodlr<float>(g, chi, hp, h, st, h->h32);
                 h->bytes = h->h32.bytes;
+                if (s == LSW_OK && hp->prec == LSW_BF16) {
+                    s = to_bf16(h->h32, h->hb, st);
+                    if (s == LSW_OK) {
+                        h->h32.release();
+                        h->bf16 = true;
+                        h->bytes = h->hb.bytes;
+                    }
+                }
             }
         }
     }
@@ -1170,6 +1321,7 @@ lsw_status lsw_destroy_hmatrix(lsw_hmatrix* h) {
     if (!h) return LSW_ERR_INVALID_ARG;
     h->h32.release();
     h->h64.release();
+    h->hb.release();
     if (h->perm_d) cudaFree(h->perm_d);
     if (h->smwU) cudaFree(h->smwU);
     if (h->smwW) cudaFree(h->smwW);

@@ -228,6 +228,11 @@ void tc_gemm_enable(bool on);
 bool tc_gemm_fits(int M, int N, int K);
 lsw_status cgemm_tc(const float2* A, int lda, long long sA, const float2* B, int ldb, long long sB, float2* C, int ldc,
                     long long sC, int M, int N, int K, float2 alpha, int batch, cudaStream_t st);
+// The same with A stored as BF16 (re, im) pairs, one 32-bit word per entry
+// (kind::f16 MMAs, B split into BF16 hi + lo): M % 128 == 0, K % 32 == 0.
+bool tc_bf16_fits(int M, int N, int K);
+lsw_status cgemm_tc_bf16(const uint32_t* A, int lda, long long sA, const float2* B, int ldb, long long sB, float2* C,
+                         int ldc, long long sC, int M, int N, int K, float2 alpha, int batch, cudaStream_t st);
 
 // Per-field FP64 squared 2-norms: out[b] = sum |x_b|^2 over n entries.
 template <typename R>

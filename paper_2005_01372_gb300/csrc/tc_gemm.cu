@@ -21,6 +21,8 @@
 // which the producer waits on (bounded) before reusing that buffer.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include <atomic>
 #include <cstdint>
 
@@ -239,6 +241,162 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
+// ---------------------------------------------------------------- BF16 A
+// The same product with A stored as BF16 pairs (re, im) and B, C in FP32:
+// kind::f16 MMAs (BF16 inputs, FP32 accumulation in TMEM).  B is split into
+// BF16 hi + lo (two products), so the result carries A's BF16 rounding and
+// hardly any of B's.  A stage is 32 complex K (64 BF16 = 128 B per row of
+// A''): the tiles keep the byte layout of the TF32 kernel.
+constexpr int TB_KC = 32;                          // complex K per stage
+constexpr int TB_A = TC_M * 2 * TB_KC * 2;         // 16 KB
+constexpr int TB_B = TC_NN * 2 * TB_KC * 2;        // 8 KB
+constexpr int TB_STAGE = TB_A + 2 * TB_B;          // A, B hi, B lo
+constexpr int TB_SMEM = 2 * TB_STAGE + 64;
+// D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), K-major, N / 8, M / 16
+constexpr uint32_t TB_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NN >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(tmem), "l"(da), "l"(db), "r"(TB_IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void split_bf16(float x, float& hi, float& lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(x));
+    lo = x - hi;
+}
+
+__global__ void __launch_bounds__(128)
+k_cgemm_tc_bf16(const uint32_t* __restrict__ A, int lda, long long sA, const float2* __restrict__ B, int ldb,
+                long long sB, float2* __restrict__ Cm, int ldc, long long sC, int N, int K, float2 alpha) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * TB_STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * TB_STAGE + 16);
+    int* abort_flag = reinterpret_cast<int*>(sm + 2 * TB_STAGE + 32);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.y, i0 = blockIdx.x * TC_M;
+    const uint32_t* Ab = A + b * sA + i0;          // one BF16 pair per element
+    const float2* Bb = B + b * sB;
+    float2* Cb = Cm + b * sC + i0;
+    const uint32_t mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const int S = K / TB_KC;
+    const int jb = lane, gb = warp;                // B slice: column jb, complex k 8 gb .. 8 gb + 7
+    uint32_t ra[TB_KC];
+    float2 rb[8];
+    auto gload = [&](int s) {
+        const int k0 = s * TB_KC;
+#pragma unroll
+        for (int kk = 0; kk < TB_KC; ++kk) ra[kk] = Ab[(long long)(k0 + kk) * lda + tid];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            rb[q] = jb < N ? Bb[(long long)jb * ldb + k0 + 8 * gb + q] : make_float2(0.f, 0.f);
+    };
+    gload(0);
+    int committed = 0;
+    for (int s = 0; s < S; ++s) {
+        const int buf = s & 1;
+        unsigned char* As = sm + buf * TB_STAGE;
+        unsigned char* Bhi = As + TB_A;
+        unsigned char* Blo = Bhi + TB_B;
+        if (tid == 0 && s >= 2 && !mbar_wait(buf ? mb1 : mb0, ((s - 2) >> 1) & 1)) *abort_flag = 1;
+        __syncthreads();
+        if (*abort_flag) break;
+        // A'' row tid: kgroup q (16 B) holds complex k = 4q .. 4q + 3, (re, im) each
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<uint4*>(As + kmaj(tid, q)) = make_uint4(ra[4 * q], ra[4 * q + 1], ra[4 * q + 2], ra[4 * q + 3]);
+        // B'' rows jb ([Re b; -Im b]) and jb + 32 ([Im b; Re b]), kgroups 2 gb, 2 gb + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float2 x = rb[4 * h + t];
+                float xh, xl, yh, yl;
+                split_bf16(x.x, xh, xl);
+                split_bf16(x.y, yh, yl);
+                rh[t] = pack_bf16(xh, -yh);
+                rl[t] = pack_bf16(xl, -yl);
+                ih[t] = pack_bf16(yh, xh);
+                il[t] = pack_bf16(yl, xl);
+            }
+            const int kg = 2 * gb + h;
+            *reinterpret_cast<uint4*>(Bhi + kmaj(jb, kg)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+            *reinterpret_cast<uint4*>(Blo + kmaj(jb, kg)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+            *reinterpret_cast<uint4*>(Bhi + kmaj(jb + 32, kg)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+            *reinterpret_cast<uint4*>(Blo + kmaj(jb + 32, kg)) = make_uint4(il[0], il[1], il[2], il[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (s + 1 < S) gload(s + 1);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a = smem_u32(As), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t o = ks * 256;    // 16 BF16 of K = two core matrices
+                mma_bf16(tmem, sdesc(a + o), sdesc(bh + o), (s > 0 || ks > 0) ? 1u : 0u);
+                mma_bf16(tmem, sdesc(a + o), sdesc(bl + o), 1u);
+            }
+            mma_commit(buf ? mb1 : mb0);
+        }
+        committed = s + 1;
+    }
+    if (tid == 0 && committed > 0) {
+        const int s = committed - 1;
+        if (!mbar_wait((s & 1) ? mb1 : mb0, (s >> 1) & 1)) *abort_flag = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const bool bad = *abort_flag != 0 || committed != S;
+    float d[TC_NN];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int c = 0; c < TC_NN; c += 16) tmem_ld16(taddr + c, d + c);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = warp * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j >= N) break;
+        float2 o;
+        if (bad) {
+            o = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+        } else {
+            const float re = d[j], im = d[32 + j];
+            o = make_float2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+        }
+        Cb[(long long)j * ldc + row] = o;
+    }
+    if (bad && tid == 0) atomicAdd(&g_tc_timeouts, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
 std::atomic<int> g_tc_enabled{1};
 
 }  // namespace
@@ -259,6 +417,23 @@ lsw_status cgemm_tc(const float2* A, int lda, long long sA, const float2* B, int
     KTimer kt("leaf_tc", st, 8.0 * ((double)batch * M * K + (double)batch * K * N + (double)batch * M * N),
               8.0 * (double)batch * M * N * K);
     k_cgemm_tc<<<dim3(M / TC_M, batch), 128, TC_SMEM, st>>>(A, lda, sA, B, ldb, sB, C, ldc, sC, N, K, alpha);
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+bool tc_bf16_fits(int M, int N, int K) { return M > 0 && M % TC_M == 0 && K > 0 && K % TB_KC == 0 && N >= 1 && N <= 32; }
+
+lsw_status cgemm_tc_bf16(const uint32_t* A, int lda, long long sA, const float2* B, int ldb, long long sB, float2* C,
+                         int ldc, long long sC, int M, int N, int K, float2 alpha, int batch, cudaStream_t st) {
+    if (!tc_bf16_fits(M, N, K) || batch <= 0 || batch > 65535) return LSW_ERR_INVALID_ARG;
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        LSW_CUDA(cudaFuncSetAttribute(k_cgemm_tc_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM));
+        attr.store(true);
+    }
+    KTimer kt("leaf_tc", st, 4.0 * (double)batch * M * K + 8.0 * ((double)batch * K * N + (double)batch * M * N),
+              8.0 * (double)batch * M * N * K);
+    k_cgemm_tc_bf16<<<dim3(M / TC_M, batch), 128, TB_SMEM, st>>>(A, lda, sA, B, ldb, sB, C, ldc, sC, N, K, alpha);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }

@@ -17,7 +17,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblsw.so")
 
-C128, C64, MIXED = 0, 1, 2
+C128, C64, MIXED, BF16 = 0, 1, 2, 3
 OP_FORWARD, OP_RESIDUAL, OP_PLAIN, OP_ADJOINT = 0, 1, 2, 3
 H_LOWRANK_SMW, H_HODLR = 0, 1
 SERIES, FGMRES = 0, 1

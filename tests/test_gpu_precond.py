@@ -294,3 +294,56 @@ def test_hodlr_power_iteration_parity_c128(lsw):
     x = media.complex_field(rng, (3, P.n))
     y = lsw.apply_precond(H, torch.from_numpy(x).cuda()).cpu().numpy()
     assert _rel(y, ref.apply(x.T).T) < 1e-10
+
+
+@pytest.mark.parametrize("n,L,k", [(64, 2, 32), (64, 2, 40), (32, 4, 5)])
+def test_bf16_storage_matches_fp32_storage(lsw, n, L, k):
+    """H built in FP32 and kept as BF16 (re, im) pairs: every stored entry is
+    rounded to 8 significant bits (relative error <= 2^-9 ~ 2e-3), and the
+    leaf inverses' cancellation amplifies that about tenfold in the product,
+    so the BF16 apply sits within 3e-2 of the FP32 apply of the same build
+    and clearly away from it (> 1e-5: the factors really are rounded).  At
+    n = 64 the leaves (1024 rows) run on the tensor cores (kind::f16); at
+    n = 32 with 4 levels (64-row leaves) on the CUDA cores, and the two
+    engines on BF16 storage agree to FP32 accuracy.  The storage takes about half the bytes."""
+    P, G, chi = _setup(lsw, n, n, seed=17, freq=12.0)
+    hp = dict(kind=lsw.H_HODLR, levels=L, rank=12, oversample=6, seed=41)
+    H32 = lsw.build_hmatrix(G, chi, lsw.HParams(prec=lsw.C64, **hp))
+    H16 = lsw.build_hmatrix(G, chi, lsw.HParams(prec=lsw.BF16, **hp))
+    assert H16.nbytes() < 0.51 * H32.nbytes()
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(media.complex_field(rng, (k, n * n)).astype(np.complex64)).cuda()
+    y32 = lsw.apply_precond(H32, x).cpu().numpy()
+    try:
+        lsw.set_tensor_cores(True)
+        y16 = lsw.apply_precond(H16, x).cpu().numpy()
+        lsw.set_tensor_cores(False)
+        y16cc = lsw.apply_precond(H16, x).cpu().numpy()
+    finally:
+        lsw.set_tensor_cores(True)
+    assert np.all(np.isfinite(y16))
+    assert 1e-5 < _rel(y16, y32) < 3e-2
+    assert _rel(y16, y16cc) < 5e-5
+
+
+def test_salt_256_bf16_hodlr_fgmres_certified(lsw):
+    """The 256 x 256 salt problem with H kept in BF16 inside mixed FGMRES:
+    the coarser preconditioner costs iterations, not accuracy; the oracle's
+    FP64 operator certifies 1e-6."""
+    wl = media.layered_salt(256, 15.0, 32, 2)
+    P, G, chi = _setup(lsw, 256, 256, velocity=wl.velocity, freq=wl.freq_hz)
+    H = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=lsw.BF16, levels=6, rank=20, oversample=10,
+                                              seed=1002))
+    pos = wl.sources[:4]
+    u0 = G.point_sources(pos, lsw.C128)
+    u, infos = lsw.solve_series(G, chi, H, u0, sp=lsw.SolveParams(prec=lsw.MIXED, method=lsw.FGMRES, tol=1e-6,
+                                                                      inner_tol=1e-3, restart=30, max_iter=60))
+    assert all(i.status == 0 for i in infos), [(i.status, i.rel_residual, i.iterations) for i in infos]
+    res = P.rel_residual(u.cpu().numpy().T, P.sources(pos))
+    assert np.all(res < 1e-6)
+
+
+def test_bf16_storage_rejected_for_smw(lsw):
+    P, G, chi = _setup(lsw, 16, 16, seed=2)
+    with pytest.raises(Exception):
+        lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_LOWRANK_SMW, prec=lsw.BF16, rank=8, oversample=4))
