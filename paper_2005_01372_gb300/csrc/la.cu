@@ -571,6 +571,169 @@ __device__ void hh_qr(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* Rou
     }
 }
 
+// The same factorisation for k <= 32 columns and m <= 2 NT rows (every
+// thread owns rows t and t + NT), with each column's update fused into the
+// pass that gathers the next column's reductions:
+//   factorisation: every thread forms the reflector of column j from the
+//     sums (alpha, ||x||^2, x^H a_c); threads t < k - j - 1 put
+//     w_c = conj(tau) v^H a_c in shared memory and R's row j in Rout (row j
+//     of A is not written during step j); one pass then scales v, updates
+//     the trailing columns of each row and accumulates ||x'||^2 and x'^H a'_c
+//     of the next column;
+//   explicit Q = H_0 ... H_{k-1} [I; 0], from j = k-1 down: rows < j of the
+//     columns > j are still zero, so w_c = tau v_j^H q_c is tau times the
+//     sums of the previous pass; one pass forms column j, updates columns
+//     > j and accumulates v_{j-1}^H q_c for the next step.
+// One pass per column in each half (hh_qr makes two), three and two
+// barriers per column (hh_qr four and three); the arithmetic and its order
+// are the same.  Rout (k x k, column-major) is required.
+template <typename R, int NT>
+__device__ void hh_qr32(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* Rout) {
+    typedef typename Cx<R>::T C;
+    __shared__ C red[(NT / 32) * 32];
+    __shared__ C sums[32];
+    __shared__ C wv[32];
+    __shared__ C tau_s[32];
+    const int kk = min(k, m);
+    for (int e = threadIdx.x; e < k * k; e += NT) Rout[e] = czero<C>();
+    C acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = czero<C>();
+    // column 0: ||x||^2 in slot 31, x^H a_c in slot c - 1
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int i = threadIdx.x + s * NT;
+        if (i >= m || i == 0) continue;
+        const C x = A[i];
+        acc[31].x += x.x * x.x + x.y * x.y;
+#pragma unroll
+        for (int q = 0; q < 31; ++q)
+            if (q < k - 1) cfmac(acc[q], x, A[(long long)(1 + q) * m + i]);
+    }
+    cta_sum32<C, NT>(acc, red, sums);
+    // ---- factorisation
+    for (int j = 0; j < kk; ++j) {
+        const int nc = k - j - 1;
+        const C alpha = A[(long long)j * m + j];
+        const R xnorm2 = sums[31].x;
+        C tau = czero<C>(), scale = czero<C>();
+        R beta = alpha.x;
+        if (!(xnorm2 == 0 && alpha.y == 0)) {
+            const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+            beta = alpha.x >= 0 ? -nrm : nrm;
+            tau = mk((beta - alpha.x) / beta, -alpha.y / beta);
+            const C d = mk(alpha.x - beta, alpha.y);
+            const R den = d.x * d.x + d.y * d.y;
+            scale = mk(d.x / den, -d.y / den);
+        }
+        if (threadIdx.x < nc) {
+            // w_c = conj(tau) (a_c[j] + conj(s) x^H a_c), c = j + 1 + t
+            const int t = threadIdx.x;
+            const C ajc = A[(long long)(j + 1 + t) * m + j];
+            const C w = cmulc(tau, cadd(ajc, cmulc(scale, sums[t])));
+            wv[t] = w;
+            Rout[(j + 1 + t) * k + j] = csub(ajc, w);
+        }
+        if (threadIdx.x == 0) {
+            Rout[j * k + j] = mk(beta, (R)0);
+            tau_s[j] = tau;
+        }
+        __syncthreads();   // wv complete
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = czero<C>();
+        C v[2], x[2];
+        bool act[2], nxt[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int i = threadIdx.x + s * NT;
+            act[s] = i < m && i > j;
+            nxt[s] = act[s] && i > j + 1;
+            v[s] = x[s] = czero<C>();
+            if (act[s]) {
+                v[s] = cmul(A[(long long)j * m + i], scale);
+                A[(long long)j * m + i] = v[s];
+            }
+        }
+        if (nc > 0) {
+            const C w0 = wv[0];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                if (!act[s]) continue;
+                C* a = A + (long long)(j + 1) * m + threadIdx.x + s * NT;
+                x[s] = csub(*a, cmul(v[s], w0));
+                *a = x[s];
+                if (nxt[s]) acc[31].x += x[s].x * x[s].x + x[s].y * x[s].y;
+            }
+#pragma unroll
+            for (int q = 0; q < 30; ++q) {
+                if (q < nc - 1) {
+                    const C w = wv[q + 1];
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        if (!act[s]) continue;
+                        C* a = A + (long long)(j + 2 + q) * m + threadIdx.x + s * NT;
+                        const C y = csub(*a, cmul(v[s], w));
+                        *a = y;
+                        if (nxt[s]) cfmac(acc[q], x[s], y);
+                    }
+                }
+            }
+        }
+        if (j + 1 < kk) cta_sum32<C, NT>(acc, red, sums);   // its first barrier also retires wv
+        else __syncthreads();
+    }
+    // ---- explicit Q; columns kk.. are zero (more columns than rows)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int i = threadIdx.x + s * NT;
+        if (i < m)
+            for (int c = kk; c < k; ++c) A[(long long)c * m + i] = czero<C>();
+    }
+    for (int j = kk - 1; j >= 0; --j) {
+        const C tau = tau_s[j];
+        const int nc = k - j - 1;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = czero<C>();
+        C v[2], vn[2];
+        bool act[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int i = threadIdx.x + s * NT;
+            act[s] = i < m && i >= j;
+            v[s] = vn[s] = czero<C>();
+            if (i < m && i < j) A[(long long)j * m + i] = czero<C>();
+            if (!act[s]) continue;
+            C* aj = A + (long long)j * m + i;
+            v[s] = i == j ? mk((R)1, (R)0) : *aj;
+            const C qj = i == j ? mk((R)1 - tau.x, -tau.y)
+                                : mk(-(tau.x * v[s].x - tau.y * v[s].y), -(tau.x * v[s].y + tau.y * v[s].x));
+            *aj = qj;
+            if (j > 0) {
+                vn[s] = A[(long long)(j - 1) * m + i];
+                cfmac(acc[0], vn[s], qj);
+            }
+        }
+        if (j < kk - 1) {   // the columns > j hold Q's partial product
+#pragma unroll
+            for (int q = 0; q < 31; ++q) {
+                if (q < nc) {
+                    const C w = cmul(tau, sums[q]);
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        if (!act[s]) continue;
+                        C* a = A + (long long)(j + 1 + q) * m + threadIdx.x + s * NT;
+                        const C y = csub(*a, cmul(v[s], w));
+                        *a = y;
+                        if (j > 0) cfmac(acc[q + 1], vn[s], y);
+                    }
+                }
+            }
+        }
+        if (j > 0) cta_sum32<C, NT>(acc, red, sums);
+    }
+    __syncthreads();
+}
+
 // Chunk step of TSQR: rows [r0, r1) of block b (chunk ch of nch, sizes as
 // even as possible) are factored in shared memory; Q_chunk replaces them and
 // R_chunk goes to rows ch*k.. of the stacked matrix S_b ((nch*k) x k).
@@ -591,7 +754,17 @@ k_tsqr_chunk(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA, i
         As[e] = A[(long long)j * m + r0 + i];
     }
     __syncthreads();
-    hh_qr<R, NT>(As, cc, k, Rs);
+    // (FP64 at 512 threads keeps hh_qr: 32 double2 sums already fill the
+    // 128 registers a thread has there)
+    if constexpr (sizeof(R) == 4 || NT <= 128) {
+        if (k <= 32 && cc <= 2 * NT) {
+            hh_qr32<R, NT>(As, cc, k, Rs);
+        } else {
+            hh_qr<R, NT>(As, cc, k, Rs);
+        }
+    } else {
+        hh_qr<R, NT>(As, cc, k, Rs);
+    }
     const int ms = nch * k;
     C* S = Sall + (long long)b * ms * k;
     for (int e = threadIdx.x; e < k * k; e += NT) {
@@ -634,12 +807,6 @@ k_tsqr_apply(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA, i
         for (int t = 0; t < k; ++t) cfma(acc, As[t * cc + i], Ts[j * k + t]);
         A[(long long)j * m + r0 + i] = acc;
     }
-}
-
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT)
-k_householder_qr(typename Cx<R>::T* __restrict__ Aall, int m, int k, long long sA) {
-    hh_qr<R, NT>(Aall + blockIdx.x * sA, m, k, nullptr);
 }
 
 // --------------------------------------------- Jacobi eigen (Hermitian)
