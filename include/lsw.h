@@ -286,6 +286,60 @@ lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hpar
                              const lsw_solve_params* sp, int max_concurrent,
                              lsw_solve_info* info, void* stream);
 
+/* Rank policy of a frequency sweep (Sec. 3.1): a frequency whose solve
+ * does not converge within the iteration limit (the paper: 30) is rebuilt
+ * with rank + rank_step and solved again from psi0; one that converges but
+ * needs more than raise_iters iterations (the paper: 10) hands rank +
+ * rank_step to the next frequency.  Ranks never exceed rank_max. */
+typedef struct {
+    int32_t rank0;        /* rank at the first frequency (>= 1)               */
+    int32_t rank_step;    /* added on each increase (>= 1)                    */
+    int32_t rank_max;     /* largest rank (>= rank0; rank_max + oversample <= 64) */
+    int32_t raise_iters;  /* iteration count above which the next frequency
+                             starts at a higher rank (>= 0)                    */
+} lsw_sweep_policy;
+
+/* Outcome of one frequency of a sweep. */
+typedef struct {
+    double freq_hz;
+    int32_t rank;            /* rank of the H behind the final solve           */
+    int32_t builds;          /* preconditioners built at this frequency        */
+    int32_t converged;       /* sources that met sp->tol                       */
+    int32_t max_iterations;  /* largest iteration count over the sources       */
+    double max_rel_residual; /* largest final FP64 relative residual           */
+    int32_t status;          /* LSW_OK, or the first failing source's status   */
+    int32_t next_rank;       /* rank handed to the next frequency              */
+} lsw_sweep_info;
+
+/* One decision of the policy (host only, no GPU work): after a solve at
+ * `rank` that returned solve_status (LSW_OK when every source converged)
+ * with largest iteration count max_iterations, *rebuild = 1 and *next_rank
+ * = the rank to rebuild with at this frequency, or *rebuild = 0 and
+ * *next_rank = the rank for the next frequency.  A failed solve at
+ * rank_max is not rebuilt.  LSW_ERR_INVALID_ARG for a NULL pointer, an
+ * invalid policy or rank < 1. */
+lsw_status lsw_sweep_next_rank(const lsw_sweep_policy* pol, int32_t rank, int32_t solve_status,
+                               int32_t max_iterations, int32_t* next_rank, int32_t* rebuild);
+
+/* The paper's frequency sweep (Sec. 3.1) on one grid: the frequencies are
+ * solved in the order given (the paper goes from the lowest, the easiest
+ * to approximate, upwards), each with its own Green table, contrast (Eq. 1),
+ * point sources and HODLR preconditioner (*hp, with hp->rank and
+ * hp->rank_max replaced by the policy's ranks), by lsw_solve_series with
+ * *sp, ranks following *pol.  grid->freq_hz is ignored; freqs_hz: HOST,
+ * nfreq values.  velocity: device, nz * nx (strip order).  sources: HOST,
+ * 2 * nsrc int32 (iz, ix).  u: device output, nfreq * nsrc fields, frequency
+ * major (complex128 for LSW_C128 / LSW_MIXED, complex64 for LSW_C64).
+ * info: HOST, nfreq records; sinfo (HOST, nfreq * nsrc, may be NULL): each
+ * source's final lsw_solve_info.  Synchronises the stream.  Returns LSW_OK
+ * when every frequency converged, else the first failing frequency's
+ * status; an error other than non-convergence, divergence or a non-finite
+ * residual ends the sweep at once. */
+lsw_status lsw_solve_sweep(const lsw_grid* grid, const double* velocity, const double* freqs_hz, int nfreq,
+                           const int32_t* sources, int nsrc, const lsw_hparams* hp,
+                           const lsw_sweep_policy* pol, const lsw_solve_params* sp, void* u,
+                           lsw_sweep_info* info, lsw_solve_info* sinfo, void* stream);
+
 /* Measure the operator's pass variants for this grid and precision on
  * nbatch fields -- 0: register radix-8 FFT passes, 1: the same with
  * 512-thread row blocks in the x pass, 2: shared-memory Stockham passes --

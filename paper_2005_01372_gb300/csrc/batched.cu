@@ -207,4 +207,100 @@ lsw_status lsw_solve_batched(const lsw_problem* probs, int nprob, const lsw_hpar
     return LSW_OK;
 }
 
+lsw_status lsw_sweep_next_rank(const lsw_sweep_policy* pol, int32_t rank, int32_t solve_status,
+                               int32_t max_iterations, int32_t* next_rank, int32_t* rebuild) {
+    if (!pol || !next_rank || !rebuild || rank < 1 || pol->rank0 < 1 || pol->rank_step < 1 ||
+        pol->rank_max < pol->rank0 || pol->raise_iters < 0)
+        return LSW_ERR_INVALID_ARG;
+    const int32_t grown = std::min(rank + pol->rank_step, pol->rank_max);
+    if (solve_status != LSW_OK) {
+        // not converged within the limit: a larger rank, from psi0 again
+        *rebuild = grown > rank ? 1 : 0;
+        *next_rank = *rebuild ? grown : rank;
+    } else {
+        // converged, but slowly: the next frequency starts higher
+        *rebuild = 0;
+        *next_rank = max_iterations > pol->raise_iters ? std::max(grown, rank) : rank;
+    }
+    return LSW_OK;
+}
+
+lsw_status lsw_solve_sweep(const lsw_grid* grid, const double* velocity, const double* freqs_hz, int nfreq,
+                           const int32_t* sources, int nsrc, const lsw_hparams* hp, const lsw_sweep_policy* pol,
+                           const lsw_solve_params* sp, void* u, lsw_sweep_info* info, lsw_solve_info* sinfo,
+                           void* stream) {
+    if (!grid || !velocity || nfreq < 0 || (nfreq > 0 && !freqs_hz) || !sources || nsrc <= 0 || !hp || !pol || !sp ||
+        !u || !info)
+        return LSW_ERR_INVALID_ARG;
+    if (hp->kind != LSW_H_HODLR || pol->rank0 < 1 || pol->rank_step < 1 || pol->rank_max < pol->rank0 ||
+        pol->raise_iters < 0 || hp->oversample < 0 || pol->rank_max + hp->oversample > 64)
+        return LSW_ERR_INVALID_ARG;
+    if (nfreq == 0) return LSW_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const long long n = (long long)grid->nz * grid->nx;
+    const int upcast = sp->prec == LSW_C64 ? LSW_C64 : LSW_C128;
+    const size_t elem = upcast == LSW_C128 ? sizeof(double2) : sizeof(float2);
+    DevBuf chi, u0;
+    LSW_TRY(chi.alloc(sizeof(double) * n, s));
+    LSW_TRY(u0.alloc(elem * n * nsrc, s));
+    std::vector<lsw_solve_info> si(nsrc);
+    lsw_hparams hpl = *hp;
+    hpl.rank_max = 0;
+    int32_t rank = pol->rank0;
+    lsw_status first_fail = LSW_OK;
+    for (int f = 0; f < nfreq; ++f) {
+        lsw_grid gf = *grid;
+        gf.freq_hz = freqs_hz[f];
+        lsw_green* g = nullptr;
+        LSW_TRY(lsw_build_green(&gf, s, &g));
+        struct GreenGuard {
+            lsw_green* g;
+            cudaStream_t s;
+            ~GreenGuard() {
+                cudaStreamSynchronize(s);
+                lsw_destroy_green(g);
+            }
+        } guard{g, s};
+        LSW_TRY(lsw_contrast(g, velocity, chi.as<double>(), s));
+        LSW_TRY(lsw_point_sources(g, sources, nsrc, upcast, u0.p, s));
+        void* uf = static_cast<char*>(u) + (size_t)f * nsrc * n * elem;
+        lsw_sweep_info& inf = info[f];
+        inf = lsw_sweep_info{};
+        inf.freq_hz = freqs_hz[f];
+        lsw_status st;
+        for (;;) {
+            hpl.rank = rank;
+            lsw_hmatrix* h = nullptr;
+            LSW_TRY(lsw_build_hmatrix(g, chi.as<double>(), &hpl, s, &h));
+            ++inf.builds;
+            st = lsw_solve_series(g, chi.as<double>(), h, u0.p, uf, nsrc, sp, si.data(), s);
+            lsw_destroy_hmatrix(h);
+            if (st != LSW_OK && st != LSW_ERR_NOT_CONVERGED && st != LSW_ERR_DIVERGED && st != LSW_ERR_NUMERIC)
+                return st;
+            int32_t maxit = 0, conv = 0;
+            double maxres = 0;
+            for (const auto& x : si) {
+                maxit = std::max(maxit, x.iterations);
+                conv += x.status == LSW_OK;
+                maxres = std::max(maxres, x.rel_residual);
+            }
+            int32_t next = rank, rebuild = 0;
+            LSW_TRY(lsw_sweep_next_rank(pol, rank, st, maxit, &next, &rebuild));
+            inf.rank = rank;
+            inf.converged = conv;
+            inf.max_iterations = maxit;
+            inf.max_rel_residual = maxres;
+            inf.status = st;
+            inf.next_rank = next;
+            rank = next;
+            if (!rebuild) break;
+        }
+        if (sinfo)
+            for (int i = 0; i < nsrc; ++i) sinfo[(size_t)f * nsrc + i] = si[i];
+        if (st != LSW_OK && first_fail == LSW_OK) first_fail = st;
+    }
+    LSW_CUDA(cudaStreamSynchronize(s));
+    return first_fail;
+}
+
 }  // extern "C"

@@ -64,6 +64,17 @@ class SolveInfo(ctypes.Structure):
                 ("fallback", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
 
 
+class _SweepPolicy(ctypes.Structure):
+    _fields_ = [("rank0", ctypes.c_int32), ("rank_step", ctypes.c_int32), ("rank_max", ctypes.c_int32),
+                ("raise_iters", ctypes.c_int32)]
+
+
+class SweepInfo(ctypes.Structure):
+    _fields_ = [("freq_hz", ctypes.c_double), ("rank", ctypes.c_int32), ("builds", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("max_iterations", ctypes.c_int32),
+                ("max_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("next_rank", ctypes.c_int32)]
+
+
 class _FnoParams(ctypes.Structure):
     _fields_ = [("nz", ctypes.c_int32), ("nx", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("modes", ctypes.c_int32), ("layers", ctypes.c_int32), ("pad_", ctypes.c_int32),
@@ -98,6 +109,12 @@ _SIGS = {
                                ctypes.POINTER(SolveInfo), VP]),
     "lsw_solve_batched": (I32, [VP, I32, ctypes.POINTER(_HParams), ctypes.POINTER(_SolveParams), I32,
                                 ctypes.POINTER(SolveInfo), VP]),
+    "lsw_sweep_next_rank": (I32, [ctypes.POINTER(_SweepPolicy), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "lsw_solve_sweep": (I32, [ctypes.POINTER(_Grid), VP, ctypes.POINTER(ctypes.c_double), I32,
+                              ctypes.POINTER(ctypes.c_int32), I32, ctypes.POINTER(_HParams),
+                              ctypes.POINTER(_SweepPolicy), ctypes.POINTER(_SolveParams), VP,
+                              ctypes.POINTER(SweepInfo), ctypes.POINTER(SolveInfo), VP]),
     "lsw_autotune": (I32, [VP, I32, I32, VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "lsw_set_tensor_cores": (I32, [I32]),
     "lsw_set_graphs": (I32, [I32]),
@@ -414,6 +431,48 @@ def solve_batched(problems, hp: HParams = None, sp: SolveParams = None, max_conc
         res.append([infos[k + j] for j in range(len(p["sources"]))])
         k += len(p["sources"])
     return outs, res
+
+
+@dataclass
+class SweepPolicy:
+    """lsw_sweep_policy: the rank rule of a frequency sweep (the paper's
+    limits: 30 iterations before a rebuild, 10 before raising the rank)."""
+    rank0: int = 10
+    rank_step: int = 10
+    rank_max: int = 50
+    raise_iters: int = 10
+
+    def c(self) -> _SweepPolicy:
+        return _SweepPolicy(self.rank0, self.rank_step, self.rank_max, self.raise_iters)
+
+
+def sweep_next_rank(pol: SweepPolicy, rank: int, solve_status: int, max_iterations: int):
+    """lsw_sweep_next_rank (host only): (next_rank, rebuild)."""
+    nxt, reb = ctypes.c_int32(), ctypes.c_int32()
+    pc = pol.c()
+    _check(lib().lsw_sweep_next_rank(ctypes.byref(pc), rank, solve_status, max_iterations, ctypes.byref(nxt),
+                                     ctypes.byref(reb)), "lsw_sweep_next_rank")
+    return nxt.value, bool(reb.value)
+
+
+def solve_sweep(nz: int, nx: int, h: float, c0: float, velocity, freqs_hz, sources, hp: HParams,
+                pol: SweepPolicy, sp: SolveParams = None, stream=None):
+    """lsw_solve_sweep.  Returns (u of shape (nfreq, nsrc, n), list of
+    SweepInfo, list per frequency of lists of SolveInfo)."""
+    sp = sp or SolveParams(prec=MIXED)
+    nf, ns, n = len(freqs_hz), len(sources), nz * nx
+    u = torch.empty((nf, ns, n), dtype=_cdtype(sp.prec), device="cuda")
+    fr = (ctypes.c_double * max(1, nf))(*[float(f) for f in freqs_hz])
+    src = (ctypes.c_int32 * (2 * ns))(*[int(v) for s_ in sources for v in s_])
+    info = (SweepInfo * max(1, nf))()
+    sinfo = (SolveInfo * max(1, nf * ns))()
+    grid = _Grid(nz, nx, h, c0, 0.0)
+    hpc, pc, spc = hp.c(), pol.c(), sp.c()
+    st = lib().lsw_solve_sweep(ctypes.byref(grid), _ptr(velocity, torch.float64), fr, nf, src, ns, ctypes.byref(hpc),
+                               ctypes.byref(pc), ctypes.byref(spc), _ptr(u), info, sinfo, _stream(stream))
+    if st not in (0, 5, 6, 7):
+        _check(st, "lsw_solve_sweep")
+    return u, [info[i] for i in range(nf)], [[sinfo[f * ns + j] for j in range(ns)] for f in range(nf)]
 
 
 FNO_WEIGHTS, FNO_GRADS, FNO_ADAM_M, FNO_ADAM_V = 0, 1, 2, 3

@@ -186,6 +186,41 @@ def marmousi_1024(freq_hz=30.0, nsrc=16, seed=4, n=1024, h=5.0) -> Workload:
     return Workload(f"marmousi-like-{n}x{n}-{freq_hz:g}Hz-{nsrc}src", n, n, h, C0, freq_hz, c, src)
 
 
+def embed(c: np.ndarray, nz: int, nx: int, c0: float = C0) -> np.ndarray:
+    """The model c (shape (nx_m, nz_m)) at the top-left corner of an nz x nx
+    grid whose other cells have the background velocity c0 (zero contrast).
+    Cells of zero contrast do not scatter, so inside the model the solution
+    on the larger grid equals the solution on the model's own grid: a model
+    of any shape runs on power-of-two grids."""
+    nxm, nzm = c.shape
+    if nzm > nz or nxm > nx:
+        raise ValueError("the grid is smaller than the model")
+    out = np.full((nx, nz), float(c0))
+    out[:nxm, :nzm] = c
+    return out
+
+
+def marmousi_subset(freq_hz=10.0, seed=5) -> Workload:
+    """Stand-in for the paper's Marmousi2 subset (Sec. 3.1): 248 x 81 cells
+    of 15 m (x by z), layered and faulted, embedded at the top-left of a
+    256 x 128 grid (x by z); one source in the middle of the top row."""
+    rng = np.random.default_rng(seed)
+    c = marmousi_like(rng, 81, 248, 15.0, n_layers=(15, 30), vtop=1500.0, vbot=4700.0, n_faults=(3, 6))
+    return Workload(f"marmousi-subset-248x81-h15-in-256x128-{freq_hz:g}Hz", 128, 256, 15.0, C0, freq_hz,
+                    embed(c, 128, 256), ((0, 124),))
+
+
+def salt_subset(freq_hz=10.0, seed=6) -> Workload:
+    """Stand-in for the paper's 2D SEG/EAGE salt model (Sec. 3.2): 700 x 150
+    cells of 10 m (x by z), layered with a salt body, embedded at the
+    top-left of a 1024 x 256 grid (x by z); one source in the middle of the
+    top row."""
+    rng = np.random.default_rng(seed)
+    c = salt_ellipse(rng, layered(rng, 150, 700, 10.0), 10.0)
+    return Workload(f"salt-subset-700x150-h10-in-1024x256-{freq_hz:g}Hz", 256, 1024, 10.0, C0, freq_hz,
+                    embed(c, 256, 1024), ((0, 350),))
+
+
 def fno_medium(seed: int, n: int, h: float = 10.0, freq=(10.0, 25.0)):
     """A training or test medium for the learned preconditioner: 8-20 dipping
     layers (1500-4500 m/s), a salt ellipse with probability 1/2, 1-3 Gaussian

@@ -57,6 +57,9 @@ def test_binding_struct_sizes_match_header():
     assert ctypes.sizeof(lsw.SolveInfo) == 24
     # lsw_fno_params: 6 int32 + uint64
     assert ctypes.sizeof(lsw._FnoParams) == 32
+    # lsw_sweep_policy: 4 int32; lsw_sweep_info: double + 4 int32 + double + 2 int32
+    assert ctypes.sizeof(lsw._SweepPolicy) == 16
+    assert ctypes.sizeof(lsw.SweepInfo) == 40
 
 
 def test_invalid_arguments_fail_without_touching_the_gpu(libpath):
@@ -87,7 +90,8 @@ def _header_struct_fields(name):
 
 @pytest.mark.parametrize("cname,pyname", [("lsw_grid", "_Grid"), ("lsw_box", "_Box"), ("lsw_hparams", "_HParams"),
                                           ("lsw_solve_params", "_SolveParams"), ("lsw_solve_info", "SolveInfo"),
-                                          ("lsw_problem", "_Problem"), ("lsw_fno_params", "_FnoParams")])
+                                          ("lsw_problem", "_Problem"), ("lsw_fno_params", "_FnoParams"),
+                                          ("lsw_sweep_policy", "_SweepPolicy"), ("lsw_sweep_info", "SweepInfo")])
 def test_binding_struct_fields_follow_the_header(cname, pyname):
     from paper_2005_01372_gb300 import lsw
     want = _header_struct_fields(cname)

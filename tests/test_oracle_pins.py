@@ -166,6 +166,26 @@ def test_zero_contrast():
         assert np.all(A.U[key] == 0)
 
 
+def test_zero_contrast_embedding_is_exact():
+    """A model embedded in a larger grid of background velocity: cells of
+    zero contrast do not scatter, so inside the model the direct solution
+    on the larger grid equals the one on the model's own grid (the model
+    need not have power-of-two sides), and outside it is psi0 plus the field
+    the model scatters there."""
+    rng = np.random.default_rng(11)
+    c = media.random_field(rng, 12, 30)
+    Pm = op.Problem(12, 30, 15.0, media.C0, 6.0, c)
+    Pe = op.Problem(16, 32, 15.0, media.C0, 6.0, media.embed(c, 16, 32))
+    src = [(0, 15)]
+    um = solve.direct(Pm, Pm.sources(src))[:, 0]
+    ue = solve.direct(Pe, Pe.sources(src))[:, 0]
+    inside = np.array([ix * 16 + iz for ix in range(30) for iz in range(12)])
+    assert _rel(ue[inside], um) < 1e-12
+    outside = np.setdiff1d(np.arange(Pe.n), inside)
+    assert _rel(ue[outside], (Pe.sources(src)[:, 0] + Pe.G0V(ue))[outside]) < 1e-12
+    assert np.all(Pe.chi[outside] == 0)
+
+
 # ----------------------------------------- p5, p6: Born, direct, the series
 
 def test_direct_solve_residual():
