@@ -104,8 +104,8 @@ class ClockSampler:
 
 DOMINANT = "qr"
 # DRAM bytes (read + write) per k_tsqr_chunk launch, from one ncu capture of all
-# 267 launches of the benchmark's HODLR build (profiles/qr_chunk_hodlr_build_256x256.md)
-QR_TRAFFIC_PER_LAUNCH = 1463721
+# 251 launches of the benchmark's HODLR build (profiles/qr_chunk_hodlr_build_256x256.md)
+QR_TRAFFIC_PER_LAUNCH = 1571332
 
 
 def fp32_alu_peak_tflops() -> float:
