@@ -664,17 +664,28 @@ __device__ void hh_qr32(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* R
                 *a = x[s];
                 if (nxt[s]) acc[31].x += x[s].x * x[s].x + x[s].y * x[s].y;
             }
+            // columns in groups of four without a branch inside a group (four
+            // independent chains): a slot past the last column rewrites
+            // column k - 1 unchanged (w = 0) after its real update, and its
+            // sum is not kept
 #pragma unroll
-            for (int q = 0; q < 30; ++q) {
-                if (q < nc - 1) {
-                    const C w = wv[q + 1];
+            for (int q0 = 0; q0 < 30; q0 += 4) {
+                if (q0 < nc - 1) {
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        if (!act[s]) continue;
-                        C* a = A + (long long)(j + 2 + q) * m + threadIdx.x + s * NT;
-                        const C y = csub(*a, cmul(v[s], w));
-                        *a = y;
-                        if (nxt[s]) cfmac(acc[q], x[s], y);
+                    for (int d = 0; d < 4; ++d) {
+                        const int q = q0 + d;
+                        if (q >= 30) break;
+                        const bool ok = q < nc - 1;
+                        const int col = ok ? j + 2 + q : k - 1;
+                        const C w = ok ? wv[q + 1] : czero<C>();
+#pragma unroll
+                        for (int s = 0; s < 2; ++s) {
+                            if (!act[s]) continue;
+                            C* a = A + (long long)col * m + threadIdx.x + s * NT;
+                            const C y = csub(*a, cmul(v[s], w));
+                            *a = y;
+                            if (nxt[s] && ok) cfmac(acc[q], x[s], y);
+                        }
                     }
                 }
             }
@@ -714,17 +725,26 @@ __device__ void hh_qr32(typename Cx<R>::T* A, int m, int k, typename Cx<R>::T* R
             }
         }
         if (j < kk - 1) {   // the columns > j hold Q's partial product
+            // groups of four as in the factorisation (a slot past the last
+            // column rewrites column k - 1 unchanged)
 #pragma unroll
-            for (int q = 0; q < 31; ++q) {
-                if (q < nc) {
-                    const C w = cmul(tau, sums[q]);
+            for (int q0 = 0; q0 < 31; q0 += 4) {
+                if (q0 < nc) {
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        if (!act[s]) continue;
-                        C* a = A + (long long)(j + 1 + q) * m + threadIdx.x + s * NT;
-                        const C y = csub(*a, cmul(v[s], w));
-                        *a = y;
-                        if (j > 0) cfmac(acc[q + 1], vn[s], y);
+                    for (int d = 0; d < 4; ++d) {
+                        const int q = q0 + d;
+                        if (q >= 31) break;
+                        const bool ok = q < nc;
+                        const int col = ok ? j + 1 + q : k - 1;
+                        const C w = ok ? cmul(tau, sums[q]) : czero<C>();
+#pragma unroll
+                        for (int s = 0; s < 2; ++s) {
+                            if (!act[s]) continue;
+                            C* a = A + (long long)col * m + threadIdx.x + s * NT;
+                            const C y = csub(*a, cmul(v[s], w));
+                            *a = y;
+                            if (j > 0 && ok) cfmac(acc[q + 1], vn[s], y);
+                        }
                     }
                 }
             }
