@@ -860,6 +860,8 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     __shared__ int order[64];
     __shared__ int nrot;
     const double2* G = Gall + (long long)blockIdx.x * k * k;
+    // e / k for e < k * k <= 4096 by a multiply and a shift (exact for k < 256)
+    const unsigned kinv = (1u << 20) / (unsigned)k + 1u;
     if (threadIdx.x == 0) {
         double t = 0;
         for (int i = 0; i < k; ++i) t += fabs(G[i * k + i].x);
@@ -889,7 +891,13 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
             for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
                 int p, q;
                 if (i == 0) { p = m - 1; q = r; }
-                else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
+                else {
+                    // (r + i) mod (m - 1) and (r - i) mod (m - 1): both below 2 (m - 1)
+                    p = r + i;
+                    if (p >= m - 1) p -= m - 1;
+                    q = r - i + (m - 1);
+                    if (q >= m - 1) q -= m - 1;
+                }
                 if (p > q) { const int t = p; p = q; q = t; }
                 R cs = 1, sn = 0, cp = 1, spp = 0;
                 if (q < k) {
@@ -933,7 +941,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
             //            + conj(U(a',a)) [A(a',b) U(b,b) + A(a',b') U(b',b)]
             // and V <- V U in place, a pair of columns per item
             for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-                const int b = e / k, a = e - b * k;
+                const int b = (int)(((unsigned)e * kinv) >> 20), a = e - b * k;
                 const int a2 = partner[a], b2 = partner[b];
                 const C ub = us[b], ub2 = up[b];
                 const C top = cadd(cmul(A[b * k + a], ub), cmul(A[b2 * k + a], ub2));
@@ -941,7 +949,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 A2[e] = cadd(cmulc(us[a], top), cmulc(up[a], bot));
             }
             for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
-                const int i = e / k, row = e - i * k;
+                const int i = (int)(((unsigned)e * kinv) >> 20), row = e - i * k;
                 const int p = pr[i].x, q = pr[i].y;
                 if (q >= k) continue;
                 const R cs = rot[4 * i], sn = rot[4 * i + 1];
