@@ -105,7 +105,7 @@ class ClockSampler:
 DOMINANT = "qr"
 # DRAM bytes (read + write) per k_tsqr_chunk launch, from one ncu capture of all
 # 251 launches of the benchmark's HODLR build (profiles/qr_chunk_hodlr_build_256x256.md)
-QR_TRAFFIC_PER_LAUNCH = 1571332
+QR_TRAFFIC_PER_LAUNCH = 1575836
 
 
 def fp32_alu_peak_tflops() -> float:
