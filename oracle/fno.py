@@ -5,7 +5,7 @@ The paper's method builds H ~ (I - G0 V)^-1 by randomized sketches (Sec. 2.3-
 2.4).  The learned variant replaces H inside flexible GMRES (the Krylov
 comparison of Sec. 3.2) by a network trained on (residual -> correction)
 pairs that H-preconditioned solves produce; H stays as the fallback and the
-FP64 residual stays the judge.  The paper has no network; this module fixes
+FP64 residual still decides convergence.  The paper has no network; this module fixes
 the one the library implements, in plain NumPy, FP64:
 
   fields:  complex, on the nz x nx grid, strip order (ix * nz + iz)

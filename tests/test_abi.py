@@ -97,3 +97,28 @@ def test_binding_struct_fields_follow_the_header(cname, pyname):
     want = _header_struct_fields(cname)
     got = [f[0] for f in getattr(lsw, pyname)._fields_]
     assert got == want, (cname, got, want)
+
+
+def _header_enum(name):
+    """{enumerator: value} of `typedef enum { ... } name;` in lsw.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    out = {}
+    for item in m.group(1).split(","):
+        k, v = (t.strip() for t in item.split("="))
+        out[k] = int(v)
+    return out
+
+
+@pytest.mark.parametrize("cname,names", [
+    ("lsw_prec", {"LSW_C128": "C128", "LSW_C64": "C64", "LSW_MIXED": "MIXED", "LSW_BF16": "BF16"}),
+    ("lsw_h_kind", {"LSW_H_LOWRANK_SMW": "H_LOWRANK_SMW", "LSW_H_HODLR": "H_HODLR"}),
+])
+def test_binding_constants_follow_the_header(cname, names):
+    from paper_2005_01372_gb300 import lsw
+    enum = _header_enum(cname)
+    assert set(enum) == set(names), (cname, sorted(enum))
+    for cn, pyn in names.items():
+        assert getattr(lsw, pyn) == enum[cn], (cn, pyn)
+
