@@ -10,6 +10,9 @@
  * Grid.      nz x nx cells of size h x h.  Unknowns are ordered in vertical
  *            strips (Sec. 2.4): the linear index of cell (iz, ix) is
  *            ix * nz + iz.  nz and nx must be powers of two, 1 <= n <= 2048.
+ *            A model of another shape is placed in such a grid whose other
+ *            cells have velocity c0: cells of zero contrast do not scatter,
+ *            so the solution inside the model is unchanged.
  * Complex.   Interleaved (re, im): LSW_C128 = two doubles, LSW_C64 = two
  *            floats.  A batch of nbatch fields is stored field after field,
  *            stride nz * nx elements.
