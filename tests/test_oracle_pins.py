@@ -390,6 +390,39 @@ def test_block_inverse_formula():
     assert _rel(printed, np.linalg.inv(Xd)[:m, m:]) > 1e-3
 
 
+def test_recompressed_inverse_is_exact_when_the_ranks_fit():
+    """Three levels of the recursive inversion with truncation at work:
+    every off-diagonal block of X has rank 1 and is stored with r = 6
+    columns, so each low-rank sum the inversion forms (2r = 12 columns) has
+    true rank at most one per ancestor level plus one, below r; Algorithm 1
+    with 4 extra probes then recovers each sum exactly, and the recursive
+    inverse equals numpy's inverse."""
+    rng = np.random.default_rng(23)
+    t = hodlr.Tree(8, 8, 3, "strips")
+    r = 6
+    X = hodlr.HODLR(t, r)
+    for c in range(8):
+        X.D[c] = np.eye(8) * 4 + media.complex_field(rng, (8, 8))
+    for l in (1, 2, 3):
+        for c in range(2 ** l):
+            m = t.size[(l, c)]
+            U = np.zeros((m, r), complex)
+            W = np.zeros((m, r), complex)
+            U[:, 0] = media.complex_field(rng, m) * 0.3
+            W[:, 0] = media.complex_field(rng, m) * 0.3
+            X.U[(l, c)], X.W[(l, c)] = U, W
+    Xd = hodlr.assemble(X)
+    Hi = hodlr.invert(X, 4, 1)
+    assert _rel(hodlr.assemble(Hi), np.linalg.inv(Xd)) < 1e-11
+    # and a rank too small for the sums (r = 1 storage of the same blocks) is not exact
+    X1 = hodlr.HODLR(t, 1)
+    X1.D = dict(X.D)
+    for key in X.U:
+        X1.U[key], X1.W[key] = X.U[key][:, :1], X.W[key][:, :1]
+    Hi1 = hodlr.invert(X1, 0, 1)
+    assert _rel(hodlr.assemble(Hi1), np.linalg.inv(Xd)) > 1e-6
+
+
 def test_hodlr_preconditioned_series_matches_lu_on_64_grid():
     """The paper's verification (Sec. 3.1): the preconditioned series gives
     the direct solution.  64 x 64 Gaussian inclusion, 10 Hz, 2 levels of
