@@ -244,7 +244,8 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     fp32_peak = fp32_alu_peak_tflops()
     dom_gbs = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    roof = {"kernel": "k_tsqr_chunk: row-chunk Householder QR of the sketch blocks (largest share of the step)",
+    roof = {"kernel": "k_tsqr_chunk: row-chunk Householder QR of the sketch blocks (largest share of the "
+                      "step in the committed launch list)",
             "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": round(dom_gbs / peak, 4), "traffic": QR_TRAFFIC_PER_LAUNCH, "launches": int(dom_n),
             "avg_launch_ms": round(dom_ms / max(1, dom_n), 4),
