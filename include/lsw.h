@@ -131,6 +131,17 @@ const char* lsw_last_error(void);
  * (diagnostics; every call's kernels are counted as they are enqueued). */
 uint64_t lsw_launch_count(void);
 
+/* Measured arithmetic peak of the current device (diagnostics, not part of
+ * the method): kind 0 = FP32 fused multiply-add, 1 = FP64; *tflops receives
+ * TFLOP/s (2 flops per FMA) of one probe kernel timed with CUDA events on
+ * stream (synchronises it).  The roofline denominators of the FP32 kernels. */
+lsw_status lsw_measure_peak(int kind, double* tflops, void* stream);
+/* The current device's default stream-ordered memory pool, from which every
+ * call of the library takes its scratch (diagnostics): bytes in use now and
+ * the high-water mark since the last reset (reset_high != 0 resets it to 0
+ * before reading). */
+lsw_status lsw_mempool_usage(uint64_t* used_current, uint64_t* used_high, int reset_high);
+
 /* Diagnostic timing of one kernel family inside any call (not part of the
  * method).  lsw_kernel_timer_start(family) resets and enables it for
  * "operator_c64" / "operator_c128" (the three FFT passes of one operator
@@ -199,9 +210,11 @@ lsw_status lsw_apply_operator(const lsw_green* g, int prec, const double* chi,
  * complex values of prec) comes from one fixed 32 MiB device array that the
  * library holds on every GPU that loads it, until the process exits; larger
  * requests return LSW_ERR_UNSUPPORTED_SIZE without launching anything.
- * The first call on a device looks up that array's device address (a runtime
- * call that allocates nothing); make that first call before any stream
- * capture.  Every call shares the one array, so calls whose work overlaps on
+ * lsw_build_green looks up that array's device address on the current
+ * device (loading the library's device code there, which commits the
+ * array, if that has not happened yet) and this call uses that address; it
+ * calls no allocating routine.  A device reset invalidates every earlier
+ * handle, and the next lsw_build_green refreshes the address.  Every call shares the one array, so calls whose work overlaps on
  * the GPU (several streams or host threads) race on it: the caller must
  * serialise them.  Nothing left by an earlier call needs clearing. */
 lsw_status lsw_apply_operator_noalloc(const lsw_green* g, int prec, const double* chi,

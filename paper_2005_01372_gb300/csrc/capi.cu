@@ -133,10 +133,58 @@ lsw_status Fork::join() {
 }
 
 lsw_status green_init(lsw_green* g, cudaStream_t st);
+lsw_status noalloc_setup();
 lsw_status contrast(const lsw_green* g, const double* vel, double* chi, cudaStream_t st);
 lsw_status point_sources(const lsw_green* g, const int32_t* pos_host, int nsrc, int prec, void* u0,
                          cudaStream_t st);
 
+}  // namespace lsw
+
+namespace lsw {
+namespace {
+// Arithmetic-peak probe: eight independent fused multiply-add chains per
+// thread, enough warps per SM to hide the pipeline latency.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T a, T b) {
+    T x0 = (T)threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+            x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+template <typename T>
+lsw_status fma_peak(int iters, double* tflops, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    LSW_CUDA(cudaGetDevice(&dev));
+    LSW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;
+    DevBuf out;
+    LSW_TRY(out.alloc(sizeof(T) * (size_t)blocks * threads, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LSW_CUDA(cudaEventCreate(&e0));
+    LSW_CUDA(cudaEventCreate(&e1));
+    k_fma_probe<T><<<blocks, threads, 0, st>>>(out.as<T>(), iters / 8 + 1, (T)0.999, (T)0.001);   // warm-up
+    LSW_LAUNCH_CHECK();
+    cudaEventRecord(e0, st);
+    k_fma_probe<T><<<blocks, threads, 0, st>>>(out.as<T>(), iters, (T)0.999, (T)0.001);
+    LSW_LAUNCH_CHECK();
+    cudaEventRecord(e1, st);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LSW_CUDA(err);
+    const double flops = 2.0 * 64.0 * (double)iters * blocks * threads;
+    *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    return LSW_OK;
+}
+}  // namespace
 }  // namespace lsw
 
 using namespace lsw;
@@ -204,6 +252,30 @@ lsw_status lsw_kernel_timer_stop(void) {
     return LSW_OK;
 }
 
+lsw_status lsw_measure_peak(int kind, double* tflops, void* stream) {
+    if (!tflops || (kind != 0 && kind != 1)) return LSW_ERR_INVALID_ARG;
+    *tflops = 0.0;
+    // about 20 ms of work at GB300 rates (78 TFLOP/s FP32, 1.25 FP64)
+    return kind == 0 ? fma_peak<float>(8192, tflops, S(stream)) : fma_peak<double>(256, tflops, S(stream));
+}
+
+lsw_status lsw_mempool_usage(uint64_t* used_current, uint64_t* used_high, int reset_high) {
+    int dev = 0;
+    LSW_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    LSW_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    if (reset_high) {
+        uint64_t zero = 0;
+        LSW_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    uint64_t cur = 0, high = 0;
+    LSW_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur));
+    LSW_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+    if (used_current) *used_current = cur;
+    if (used_high) *used_high = high;
+    return LSW_OK;
+}
+
 lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out) {
     if (!grid || !out) return LSW_ERR_INVALID_ARG;
     *out = nullptr;
@@ -231,6 +303,7 @@ lsw_status lsw_build_green(const lsw_grid* grid, void* stream, lsw_green** out) 
     g->freq = grid->freq_hz;
     g->k = 2.0 * M_PI * grid->freq_hz / grid->c0;
     lsw_status st = green_init(g, S(stream));
+    if (st == LSW_OK) st = noalloc_setup();
     if (st != LSW_OK) {
         lsw_destroy_green(g);
         return st;

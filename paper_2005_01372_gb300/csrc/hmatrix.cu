@@ -343,8 +343,9 @@ lsw_status upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 
 // ------------------------------------------------------------- truncation
 // Best rank-r part of Q Yt^H for a batch of blocks (Q: nb x rp, Yt: mb x rp):
-// with Yt^H Yt = V diag(lam) V^H (FP64 Gram, Jacobi in precision R), keep the r leading
-// eigenvectors Vr:  U = alphaU Q Vr,  W = Yt Vr,  so U W^H = alphaU Q Vr Vr^H Yt^H.
+// with Yt^H Yt = V diag(lam) V^H (FP64 Gram, FP64 eigen-decomposition), keep
+// the r leading eigenvectors Vr:  U = alphaU Q Vr,  W = Yt Vr,  so
+// U W^H = alphaU Q Vr Vr^H Yt^H.
 template <typename R>
 lsw_status truncate(const typename Cx<R>::T* Q, int nb, const typename Cx<R>::T* Yt, int mb, int rp, int r, int nblk,
                     typename Cx<R>::T alphaU, typename Cx<R>::T* Uout, long long sU, typename Cx<R>::T* Wout,
@@ -354,7 +355,7 @@ lsw_status truncate(const typename Cx<R>::T* Q, int nb, const typename Cx<R>::T*
     LSW_TRY(G.alloc(sizeof(double2) * (size_t)nblk * rp * rp, st));
     LSW_TRY(V.alloc(sizeof(C) * (size_t)nblk * rp * rp, st));
     LSW_TRY(gram64<R>(Yt, mb, rp, (long long)mb * rp, nblk, G.as<double2>(), st));
-    LSW_TRY(heev_jacobi<R>(G.as<double2>(), V.as<C>(), rp, nblk, st));
+    LSW_TRY(heev_ql<R>(G.as<double2>(), V.as<C>(), rp, nblk, st));
     const int rr = std::min(r, rp);
     if (rr < r) {
         LSW_CUDA(cudaMemsetAsync(Uout, 0, sizeof(C) * (size_t)sU * nblk, st));
@@ -367,6 +368,19 @@ lsw_status truncate(const typename Cx<R>::T* Q, int nb, const typename Cx<R>::T*
     return LSW_OK;
 }
 
+// Thin QR of the sketch blocks (Algorithm 1, step 3): FP64 Householder for
+// complex128; shifted Cholesky QR with FP64 Grams and factors for complex64.
+template <typename R>
+lsw_status qr_sketch(typename Cx<R>::T* A, int m, int k, long long sA, int batch, cudaStream_t st);
+template <>
+lsw_status qr_sketch<double>(double2* A, int m, int k, long long sA, int batch, cudaStream_t st) {
+    return qr_explicit<double>(A, m, k, sA, batch, nullptr, st);
+}
+template <>
+lsw_status qr_sketch<float>(float2* A, int m, int k, long long sA, int batch, cudaStream_t st) {
+    return qr_sketch_c64(A, m, k, sA, batch, st);
+}
+
 // ---------------------------------------------------------------- sketches
 // Randomized range finder (Algorithm 1/2) for nblk blocks of G0 V on boxes
 // of one shape.  fwd(Xin, Yout): Yout = (G0 V)[s, t] Xin for every block;
@@ -376,12 +390,12 @@ template <typename R, typename F, typename A>
 lsw_status range_finder(int ns, int nt, int rp, int q, int nblk, typename Cx<R>::T* Omega, typename Cx<R>::T* Q,
                         typename Cx<R>::T* Yt, F fwd, A adj, cudaStream_t st) {
     LSW_TRY(fwd(Omega, Q));
-    LSW_TRY(qr_explicit<R>(Q, ns, rp, (long long)ns * rp, nblk, nullptr, st));
+    LSW_TRY(qr_sketch<R>(Q, ns, rp, (long long)ns * rp, nblk, st));
     for (int it = 0; it < q; ++it) {
         LSW_TRY(adj(Q, Yt));
-        LSW_TRY(qr_explicit<R>(Yt, nt, rp, (long long)nt * rp, nblk, nullptr, st));
+        LSW_TRY(qr_sketch<R>(Yt, nt, rp, (long long)nt * rp, nblk, st));
         LSW_TRY(fwd(Yt, Q));
-        LSW_TRY(qr_explicit<R>(Q, ns, rp, (long long)ns * rp, nblk, nullptr, st));
+        LSW_TRY(qr_sketch<R>(Q, ns, rp, (long long)ns * rp, nblk, st));
     }
     return adj(Q, Yt);
 }
@@ -814,7 +828,7 @@ lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, c
                         2 * r, stt, cnt, st));
         LSW_TRY(gemm<R>('N', 'N', nb, rp, 2 * r, one<C>(), uc.as<C>(), nb, sc, tt.as<C>(), 2 * r, stt, zero<C>(),
                         ys.as<C>(), nb, sp, cnt, st));
-        LSW_TRY(qr_explicit<R>(ys.as<C>(), nb, rp, sp, cnt, nullptr, st));
+        LSW_TRY(qr_sketch<R>(ys.as<C>(), nb, rp, sp, cnt, st));
         // Yt = Wc (Uc^H Q)
         LSW_TRY(gemm<R>('C', 'N', 2 * r, rp, nb, one<C>(), uc.as<C>(), nb, sc, ys.as<C>(), nb, sp, zero<C>(), tt.as<C>(),
                         2 * r, stt, cnt, st));

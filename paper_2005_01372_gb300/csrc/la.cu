@@ -1762,6 +1762,8 @@ template <typename R>
 lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st) {
     typedef typename Cx<R>::T CT;
     if (batch <= 0 || k <= 0) return LSW_OK;
+    // complex64 data: error-free products, FP64-accurate sums (small64.cu)
+    if (sizeof(R) == 4) return gram64_c64(reinterpret_cast<const float2*>(Y), m, k, sY, batch, G, st);
     if (k > 64) return LSW_ERR_INVALID_ARG;   // 16 entries per thread at 256 threads
     const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
     DevBuf part;

@@ -206,6 +206,21 @@ lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int ba
 template <typename R>
 lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st);
 
+// FP64 small-matrix arithmetic of the sketches (small64.cu).
+// Gram matrices of complex64 blocks with error-free products (Dot2), FP64 result.
+lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st);
+// Rinv_b = R_b^-1 (upper triangular, k x k) with G_b + s I = R_b^H R_b, an
+// FP64 Cholesky factor, s = shift_rel tr(G_b) / k (raised on breakdown).
+template <typename R>
+lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st);
+// Eigenvectors of the FP64 Hermitian G_b as the columns of V_b (k x k), by
+// decreasing eigenvalue: FP64 tridiagonalisation and implicit QL.
+template <typename R>
+lsw_status heev_ql(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st);
+// Thin QR of complex64 sketch blocks (Q in place): shifted Cholesky QR3 with
+// FP64 Grams and factors, or FP64 Householder for short blocks.
+lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaStream_t st);
+
 // Cast FP64 complex -> working precision.
 template <typename R>
 lsw_status cast_from64(const double2* src, typename Cx<R>::T* dst, long long n, cudaStream_t st);

@@ -30,23 +30,45 @@ void* g_scratch_ptr[kMaxDevices] = {};
 // The array's device address on the current device.  In host code the
 // symbol's name is only a host-side stand-in: handing it to a kernel would
 // fault, or silently use the wrong memory where the GPU can reach host
-// memory, so the address is looked up once per device, with that device
-// current, and cached.
+// memory, so the address is looked up with the device current.
+lsw_status lookup_scratch(int dev, void** out) {
+    void* p = nullptr;
+    LSW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_scratch_ptr[dev] = p;
+    *out = p;
+    return LSW_OK;
+}
+
 lsw_status scratch_on_current_device(void** out) {
     int dev = 0;
     LSW_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return LSW_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        LSW_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_ptr[dev] = p;
+    if (g_scratch_ptr[dev]) {
+        *out = g_scratch_ptr[dev];
+        return LSW_OK;
     }
-    *out = g_scratch_ptr[dev];
-    return LSW_OK;
+    return lookup_scratch(dev, out);
 }
 
 }  // namespace
+
+// Set-up, once per lsw_build_green on the current device: (re)load the
+// array's address.  Looking it up also loads the library's device code on
+// that device if it was not loaded yet, which is when the array is
+// committed, so no later call of the entry point does either.  A device
+// reset invalidates every handle built before it; the next lsw_build_green
+// refreshes the address, so a cached address is never stale for a valid
+// handle.
+lsw_status noalloc_setup() {
+    int dev = 0;
+    LSW_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return LSW_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    void* p = nullptr;
+    return lookup_scratch(dev, &p);
+}
+
 }  // namespace lsw
 
 using namespace lsw;

@@ -92,6 +92,8 @@ _SIGS = {
     "lsw_kernel_timer_read": (I32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "lsw_kernel_timer_stop": (I32, []),
+    "lsw_measure_peak": (I32, [I32, ctypes.POINTER(ctypes.c_double), VP]),
+    "lsw_mempool_usage": (I32, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), I32]),
     "lsw_build_green": (I32, [ctypes.POINTER(_Grid), VP, ctypes.POINTER(VP)]),
     "lsw_destroy_green": (I32, [VP]),
     "lsw_green_table": (I32, [VP, VP, VP]),
@@ -272,6 +274,21 @@ def kernel_timer_read():
     _check(lib().lsw_kernel_timer_read(ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl), ctypes.byref(n)),
            "lsw_kernel_timer_read")
     return ms.value, by.value, fl.value, n.value
+
+
+def measure_peak(kind: int = 0, stream=None) -> float:
+    """Measured FMA peak of the current device in TFLOP/s (0: FP32, 1: FP64)."""
+    t = ctypes.c_double(0.0)
+    _check(lib().lsw_measure_peak(int(kind), ctypes.byref(t), _stream(stream)), "lsw_measure_peak")
+    return float(t.value)
+
+
+def mempool_usage(reset_high: bool = False):
+    """(bytes in use, high-water mark) of the device's default memory pool."""
+    cur, high = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().lsw_mempool_usage(ctypes.byref(cur), ctypes.byref(high), 1 if reset_high else 0),
+           "lsw_mempool_usage")
+    return int(cur.value), int(high.value)
 
 
 def kernel_timer_stop():

@@ -45,6 +45,14 @@ def test_sweep_on_embedded_model(lsw, method):
         want_next = min(inf.rank + pol.rank_step, pol.rank_max) if inf.max_iterations > pol.raise_iters else inf.rank
         assert inf.next_rank == want_next
         start = inf.next_rank
+        # Cells outside the model have zero contrast, so inside the model the
+        # residual of the embedded problem is the model's own residual: its
+        # norm is at most the embedded residual's, tol ||psi0 (embedded)||.
+        # Relative to the model's own ||psi0|| the bound is therefore
+        # tol ||psi0 (embedded)|| / ||psi0 (model)|| (times 1.001 for the
+        # rounding of two FP64 residual evaluations of the same field).
         P = oop.Problem(24, 60, h, media.C0, freqs[f], c)
+        Pe = oop.Problem(nz, nx, h, media.C0, freqs[f], media.embed(c, nz, nx))
+        bound = 1.001 * sp.tol * np.linalg.norm(Pe.sources(src)) / np.linalg.norm(P.sources(src))
         res = P.rel_residual(u[f, 0].cpu().numpy()[inside][:, None], P.sources(src))
-        assert res[0] < 3e-6, (f, res[0])
+        assert res[0] <= bound, (f, res[0], bound)

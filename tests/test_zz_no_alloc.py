@@ -44,8 +44,17 @@ def test_noalloc_matches_allocating_call_twice(lsw, prec):
         u = torch.from_numpy(media.complex_field(rng, (nb, nz * nx))).to(dt).cuda()
         u0 = torch.from_numpy(media.complex_field(rng, (nb, nz * nx))).to(dt).cuda()
         ref = lsw.apply_operator(G, chi, u, u0, modes[call])
-        got = lsw.apply_operator_noalloc(G, chi, u, u0, modes[call])
+        got = torch.empty_like(u)
         torch.cuda.synchronize()
+        # nothing is allocated during the call: neither device memory at large
+        # nor the stream-ordered pool the library's other calls draw from
+        free0 = torch.cuda.mem_get_info()[0]
+        used0, _ = lsw.mempool_usage(reset_high=True)
+        lsw.apply_operator_noalloc(G, chi, u, u0, modes[call], y=got)
+        torch.cuda.synchronize()
+        used1, high = lsw.mempool_usage()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert used1 == used0 and high <= used0, (used0, used1, high)
         assert _rel(got, ref) < TOL[prec], (call, _rel(got, ref))
 
 
