@@ -169,9 +169,17 @@ k_pass_c(const typename Cx<R>::T* __restrict__ T, DevGeom geo, int pz, int logpz
 
 // ------------------------------------------------- register-FFT passes
 // The same three passes with register-resident radix-8 line FFTs, for
-// 8 <= 2bz, 2bx <= 2048.  Here T holds, per field, bx columns of 2bz
-// entries: T[ix][kz].  Passes A and C read and write whole columns
-// (coalesced); pass B moves tiles of lpc rows through shared memory.
+// 8 <= 2bz, 2bx <= 2048.  Here T holds, per field, the 2bz x bx spectrum in
+// kz-blocks: the kblk rows kz = kblk j .. kblk j + kblk - 1 (64 bytes of one
+// column) lie next to each other for ix = 0, 1, ..., bx - 1, and the blocks
+// follow each other.  A column's write (pass A) and read (pass C) then move
+// whole 64-byte segments, and pass B reads and writes every kz-block as one
+// contiguous run.
+template <typename C> __host__ __device__ constexpr int kblk() { return 64 / (int)sizeof(C); }
+template <typename C> __device__ __forceinline__ long long tile_index(int kz, int ix, int bx) {
+    constexpr int KB = kblk<C>();
+    return (long long)(kz / KB) * bx * KB + (long long)ix * KB + (kz % KB);
+}
 template <typename R, int LOGP>
 __global__ void __launch_bounds__(256)
 k_fa(const typename Cx<R>::T* __restrict__ u, DevGeom geo, const typename Cx<R>::T* __restrict__ tw,
@@ -204,57 +212,75 @@ k_fa(const typename Cx<R>::T* __restrict__ u, DevGeom geo, const typename Cx<R>:
     }
     fft_line<C, LOGP>(v, s, t, tw, twstep, false);
     if (valid) {
-        C* Tb = T + (long long)b * pz * geo.bx + (long long)ix * pz;
+        C* Tb = T + (long long)b * pz * geo.bx;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) Tb[t + r * Tz] = v[r];
+        for (int r = 0; r < 8; ++r) Tb[tile_index<C>(t + r * Tz, ix, geo.bx)] = v[r];
     }
 }
 
+// Pass B on kz-blocks.  A CTA owns nblk consecutive kz-blocks of one field
+// (kblk rows each): it reads them as one contiguous run of memory, turns them
+// into rows of a shared-memory tile (odd row stride), runs the x transforms
+// of RC rows at a time (Tx threads per row, register radix-8 lines), and
+// writes the run back.  Rows past the field's last kz-block are transformed
+// as zeros and not stored, so every thread meets every barrier.
 template <typename R, int LOGP, int NTB>
 __global__ void __launch_bounds__(NTB)
-k_fb(typename Cx<R>::T* __restrict__ T, int pz, const typename Cx<R>::T* __restrict__ spt,
+k_fb(typename Cx<R>::T* __restrict__ T, int pz, int nblk, const typename Cx<R>::T* __restrict__ spt,
      const typename Cx<R>::T* __restrict__ tw, int twstep) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    constexpr int px = 1 << LOGP, bx = px >> 1, Tx = px >> 3, lpc = NTB / Tx;
-    constexpr int TS = bx + 4;                                   // tile row stride: conflict-free transposes
+    constexpr int px = 1 << LOGP, bx = px >> 1, Tx = px >> 3, RC = NTB / Tx;
+    constexpr int KB = kblk<C>();
+    constexpr int TS = bx + 1;                                   // odd: transposing stores spread over banks
+    C* tile = reinterpret_cast<C*>(sm_raw);                      // nblk * KB rows of TS
     const int l = threadIdx.x / Tx, t = threadIdx.x - l * Tx;
-    C* tile = reinterpret_cast<C*>(sm_raw);                      // lpc rows of bx
-    C* s = tile + lpc * TS + l * (pad8(px) + 1);
+    C* s = tile + (size_t)nblk * KB * TS + (size_t)l * (pad8(px) + 1);
     const int b = blockIdx.y;
-    const int kz0 = blockIdx.x * lpc;
-    const int nrow = min(lpc, pz - kz0);
-    C* Tb = T + (long long)b * pz * bx;
-    for (int e = threadIdx.x; e < lpc * bx; e += NTB) {
-        const int r = e % lpc, ix = e / lpc;
-        tile[r * TS + ix] = r < nrow ? Tb[(long long)ix * pz + kz0 + r] : czero<C>();
+    const int kb0 = blockIdx.x * nblk;
+    const int nb = min(nblk, pz / KB - kb0);                     // kz-blocks of this CTA
+    const int nrows = nb * KB;
+    C* run = T + (long long)b * pz * bx + (long long)kb0 * bx * KB;
+    const int nrun = nrows * bx;
+    for (int e = threadIdx.x; e < nrun; e += NTB) {
+        const int blk = e / (bx * KB), w = e - blk * (bx * KB);
+        const int ix = w / KB, r = w - ix * KB;
+        tile[(blk * KB + r) * TS + ix] = run[e];
     }
     __syncthreads();
-    const int kz = kz0 + l;
-    C v[8];
+    const int rows_all = nblk * KB;
+    for (int r0 = 0; r0 < rows_all; r0 += RC) {
+        const int row = r0 + l;
+        const bool live = row < nrows;
+        const int kz = kb0 * KB + row;
+        C v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int kx = t + q * Tx;
-        v[q] = kx < bx ? tile[l * TS + kx] : czero<C>();
-    }
-    fft_line<C, LOGP>(v, s, t, tw, twstep, false);
-    const int qzz = kz < pz ? min(kz, pz - kz) : 0;     // rows past pz are padding
-    const C* sp = spt + (long long)qzz * (bx + 1);
+        for (int q = 0; q < 8; ++q) {
+            const int kx = t + q * Tx;
+            v[q] = (live && kx < bx) ? tile[row * TS + kx] : czero<C>();
+        }
+        fft_line<C, LOGP>(v, s, t, tw, twstep, false);
+        const int qzz = live ? min(kz, pz - kz) : 0;
+        const C* sp = spt + (long long)qzz * (bx + 1);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int kx = t + q * Tx;
-        v[q] = cmul(v[q], sp[min(kx, px - kx)]);
-    }
-    fft_line<C, LOGP>(v, s, t, tw, twstep, true);
+        for (int q = 0; q < 8; ++q) {
+            const int kx = t + q * Tx;
+            v[q] = cmul(v[q], sp[min(kx, px - kx)]);
+        }
+        fft_line<C, LOGP>(v, s, t, tw, twstep, true);
+        if (live) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int kx = t + q * Tx;
-        if (kx < bx) tile[l * TS + kx] = v[q];
+            for (int q = 0; q < 8; ++q) {
+                const int kx = t + q * Tx;
+                if (kx < bx) tile[row * TS + kx] = v[q];
+            }
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < lpc * bx; e += NTB) {
-        const int r = e % lpc, ix = e / lpc;
-        if (r < nrow) Tb[(long long)ix * pz + kz0 + r] = tile[r * TS + ix];
+    for (int e = threadIdx.x; e < nrun; e += NTB) {
+        const int blk = e / (bx * KB), w = e - blk * (bx * KB);
+        const int ix = w / KB, r = w - ix * KB;
+        run[e] = tile[(blk * KB + r) * TS + ix];
     }
 }
 
@@ -271,10 +297,10 @@ k_fc(const typename Cx<R>::T* __restrict__ T, DevGeom geo, const typename Cx<R>:
     const int b = blockIdx.y;
     const int ix = blockIdx.x * lpc + l;
     const bool valid = ix < geo.bx;
-    const C* Tb = T + (long long)b * pz * geo.bx + (long long)ix * pz;
+    const C* Tb = T + (long long)b * pz * geo.bx;
     C v[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = valid ? Tb[t + r * Tz] : czero<C>();
+    for (int r = 0; r < 8; ++r) v[r] = valid ? Tb[tile_index<C>(t + r * Tz, ix, geo.bx)] : czero<C>();
     fft_line<C, LOGP>(v, s, t, tw, twstep, true);
     if (!valid) return;
     const int2 org = box_origin(geo, b);
@@ -474,13 +500,13 @@ lsw_status launch_fa(int lg, dim3 grid, size_t sm, cudaStream_t st, const typena
 }
 
 template <typename R, int NTB>
-lsw_status launch_fb(int lg, dim3 grid, size_t sm, cudaStream_t st, typename Cx<R>::T* work, int pz,
+lsw_status launch_fb(int lg, dim3 grid, size_t sm, cudaStream_t st, typename Cx<R>::T* work, int pz, int nblk,
                      const typename Cx<R>::T* spt, const typename Cx<R>::T* tw, int tws) {
     static std::atomic<bool> done[12];
     LSW_LOG_SWITCH(lg, {
         if (L_ < 4 && NTB > 256) return LSW_ERR_UNSUPPORTED_SIZE;
         LSW_TRY(set_smem(k_fb<R, L_, NTB>, done[L_]));
-        k_fb<R, L_, NTB><<<grid, NTB, sm, st>>>(work, pz, spt, tw, tws);
+        k_fb<R, L_, NTB><<<grid, NTB, sm, st>>>(work, pz, nblk, spt, tw, tws);
         LSW_LAUNCH_CHECK();
     })
     return LSW_OK;
@@ -546,14 +572,20 @@ lsw_status op_apply(const lsw_green* g, const Spectrum& sp, const OpGeom& geo, i
         const int ntb = (variant == 1 && px >= 16) ? 512 : 256;
         const int lz = 256 / (pz >> 3), lx = ntb / (px >> 3);
         const size_t smA = sizeof(C) * (size_t)lz * (pad8h(pz) + 1);
-        const size_t smB = sizeof(C) * ((size_t)lx * (bx + 4) + (size_t)lx * (pad8h(px) + 1));
+        // pass B: kz-blocks per CTA so that a CTA holds >= lx rows and about
+        // 4096 entries, within the field's pz / kblk blocks
+        constexpr int KB = kblk<C>();
+        const int nkb = pz / KB;
+        int nblk = std::max((lx + KB - 1) / KB, 4096 / (KB * bx));
+        nblk = std::max(1, std::min(nblk, nkb));
+        const size_t smB = sizeof(C) * ((size_t)nblk * KB * (bx + 1) + (size_t)lx * (pad8h(px) + 1));
         const int twz = g->twP / pz, twx = g->twP / px;
-        dim3 gA((bx + lz - 1) / lz, nbatch), gB((pz + lx - 1) / lx, nbatch);
+        dim3 gA((bx + lz - 1) / lz, nbatch), gB((nkb + nblk - 1) / nblk, nbatch);
         KTimer kt(sizeof(R) == 8 ? "operator_c128" : "operator_c64", st, op_bytes(sizeof(C), bz, bx, nbatch, u0 != nullptr, mode),
                   op_flops(bz, bx, nbatch));
         LSW_TRY(launch_fa<R>(logpz, gA, smA, st, u, dg, tw, twz, mode == LSW_OP_ADJOINT, work));
-        if (ntb == 512) LSW_TRY((launch_fb<R, 512>(logpx, gB, smB, st, work, pz, spt, tw, twx)));
-        else LSW_TRY((launch_fb<R, 256>(logpx, gB, smB, st, work, pz, spt, tw, twx)));
+        if (ntb == 512) LSW_TRY((launch_fb<R, 512>(logpx, gB, smB, st, work, pz, nblk, spt, tw, twx)));
+        else LSW_TRY((launch_fb<R, 256>(logpx, gB, smB, st, work, pz, nblk, spt, tw, twx)));
         LSW_TRY(launch_fc<R>(logpz, gA, smA, st, work, dg, tw, twz, mode, u, u0, y));
         return LSW_OK;
     }

@@ -355,7 +355,8 @@ lsw_status truncate(const typename Cx<R>::T* Q, int nb, const typename Cx<R>::T*
     LSW_TRY(G.alloc(sizeof(double2) * (size_t)nblk * rp * rp, st));
     LSW_TRY(V.alloc(sizeof(C) * (size_t)nblk * rp * rp, st));
     LSW_TRY(gram64<R>(Yt, mb, rp, (long long)mb * rp, nblk, G.as<double2>(), st));
-    LSW_TRY(heev_ql<R>(G.as<double2>(), V.as<C>(), rp, nblk, st));
+    if (sizeof(R) == 4) LSW_TRY(heev_c64(G.as<double2>(), reinterpret_cast<float2*>(V.p), rp, nblk, st));
+    else LSW_TRY(heev_jacobi<R>(G.as<double2>(), V.as<C>(), rp, nblk, st));
     const int rr = std::min(r, rp);
     if (rr < r) {
         LSW_CUDA(cudaMemsetAsync(Uout, 0, sizeof(C) * (size_t)sU * nblk, st));

@@ -843,7 +843,7 @@ template <typename R> __device__ __forceinline__ R jacobi_skip() { return sizeof
 #define JACOBI_COUNT_ROTATION atomicAdd(&nrot, 1)
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k) {
+k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int polish) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int m = (k + 1) & ~1;                 // even number of players
@@ -874,8 +874,12 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     }
     __syncthreads();
     // squared off-diagonal norm relative to the total that the precision
-    // can reach (FP32 rounding stalls near 1e-13): stop there
-    const R tol = sizeof(R) == 8 ? (R)1e-26 : (R)1e-11;
+    // can reach (FP32 rounding stalls near 1e-13): stop there.  A polishing
+    // run (a nearly diagonal input whose small eigenvalues must be resolved
+    // relative to themselves) stops only on a sweep without rotations and
+    // uses a tighter pair threshold.
+    const R tol = polish ? (R)0 : (sizeof(R) == 8 ? (R)1e-26 : (R)1e-11);
+    const R skip = polish ? (sizeof(R) == 8 ? (R)1e-15 : (R)2e-7) : jacobi_skip<R>();
     for (int sweep = 0; sweep < 40; ++sweep) {
         C part = czero<C>();
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
@@ -906,7 +910,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                     const R ac = sqrt(c.x * c.x + c.y * c.y);
                     // rotate only while the pair is not yet negligible
                     // against its diagonal (relative threshold above rounding)
-                    if (ac > jacobi_skip<R>() * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
+                    if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
                         ac > 0) {
                         JACOBI_COUNT_ROTATION;
                         const R tau = (aqq - app) / (2 * ac);
@@ -946,7 +950,9 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 const C ub = us[b], ub2 = up[b];
                 const C top = cadd(cmul(A[b * k + a], ub), cmul(A[b2 * k + a], ub2));
                 const C bot = cadd(cmul(A[b * k + a2], ub), cmul(A[b2 * k + a2], ub2));
-                A2[e] = cadd(cmulc(us[a], top), cmulc(up[a], bot));
+                // the entry a rotation annihilates is zero by construction
+                const bool killed = b == a2 && a != b && (up[a].x != 0 || up[a].y != 0);
+                A2[e] = killed ? czero<C>() : cadd(cmulc(us[a], top), cmulc(up[a], bot));
             }
             for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
                 const int i = (int)(((unsigned)e * kinv) >> 20), row = e - i * k;
@@ -987,7 +993,8 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
 #define JACOBI_COUNT_ROTATION ++nrw
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int batch) {
+k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int batch,
+                   int polish) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int m = (k + 1) & ~1;
@@ -1012,9 +1019,9 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
         V[e] = mk((R)((e % k) == (e / k) ? 1 : 0), (R)0);
     }
     __syncwarp();
-    // squared off-diagonal norm relative to the total that the precision
-    // can reach (FP32 rounding stalls near 1e-13): stop there
-    const R tol = sizeof(R) == 8 ? (R)1e-26 : (R)1e-11;
+    // the same stopping rules as the CTA version
+    const R tol = polish ? (R)0 : (sizeof(R) == 8 ? (R)1e-26 : (R)1e-11);
+    const R skip = polish ? (sizeof(R) == 8 ? (R)1e-15 : (R)2e-7) : jacobi_skip<R>();
     for (int sweep = 0; sweep < 40; ++sweep) {
         R off = 0, tot = 0;
         for (int e = lane; e < k * k; e += 32) {
@@ -1042,7 +1049,7 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
                     const R ac = sqrt(c.x * c.x + c.y * c.y);
                     // rotate only while the pair is not yet negligible
                     // against its diagonal (relative threshold above rounding)
-                    if (ac > jacobi_skip<R>() * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
+                    if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
                         ac > 0) {
                         JACOBI_COUNT_ROTATION;
                         const R tau = (aqq - app) / (2 * ac);
@@ -1082,6 +1089,15 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
                 const C eq = cmul(ep, aq);
                 A[col * k + p] = mk(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
                 A[col * k + q] = mk(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
+            }
+            __syncwarp();
+            // the entries a rotation annihilates are zero by construction
+            for (int i = lane; i < m / 2; i += 32) {
+                const int p = pr[i].x, q = pr[i].y;
+                if (q < k && rot[4 * i + 1] != (R)0) {
+                    A[q * k + p] = czero<C>();
+                    A[p * k + q] = czero<C>();
+                }
             }
             __syncwarp();
         }
@@ -1777,7 +1793,7 @@ lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int ba
 }
 
 template <typename R>
-lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st) {
+lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st, int polish) {
     typedef typename Cx<R>::T CT;
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
@@ -1792,7 +1808,7 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
     }
     if (batch >= 4 * 152) {
         // many matrices: one warp each
-        k_heev_jacobi_warp<R><<<(batch + wpc - 1) / wpc, 32 * wpc, perA * wpc, st>>>(G, V, k, batch);
+        k_heev_jacobi_warp<R><<<(batch + wpc - 1) / wpc, 32 * wpc, perA * wpc, st>>>(G, V, k, batch, polish);
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
@@ -1803,7 +1819,7 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
     }
     const size_t smb = sizeof(CT) * (3 * (size_t)k * k + 2 * (size_t)k) + sizeof(R) * 4 * (m / 2) +
                        sizeof(int2) * (m / 2) + sizeof(int) * (size_t)k;
-    k_heev_jacobi<R><<<batch, 256, smb, st>>>(G, V, k);
+    k_heev_jacobi<R><<<batch, 256, smb, st>>>(G, V, k, polish);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
@@ -2025,7 +2041,7 @@ lsw_status norms2(const typename Cx<R>::T* x, long long n, int batch, double* ou
                                 cudaStream_t);                                                                    \
     template lsw_status qr_explicit<R>(Cx<R>::T*, int, int, long long, int, Cx<R>::T*, cudaStream_t);             \
     template lsw_status gram64<R>(const Cx<R>::T*, int, int, long long, int, double2*, cudaStream_t);             \
-    template lsw_status heev_jacobi<R>(const double2*, Cx<R>::T*, int, int, cudaStream_t);                        \
+    template lsw_status heev_jacobi<R>(const double2*, Cx<R>::T*, int, int, cudaStream_t, int);                        \
     template lsw_status cast_from64<R>(const double2*, Cx<R>::T*, long long, cudaStream_t);                        \
     template lsw_status gaussian_fill<R>(Cx<R>::T*, int, int, long long, int, uint64_t, const uint32_t*,          \
                                          const uint32_t*, cudaStream_t);                                          \

@@ -202,9 +202,11 @@ lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int ba
 
 // Batched Hermitian eigenvectors by cyclic Jacobi in precision R: V_b (k x k)
 // receives the eigenvectors of the FP64 matrix G_b as columns, sorted by
-// decreasing eigenvalue.
+// decreasing eigenvalue.  polish != 0: for a nearly diagonal G whose small
+// eigenvalues are to be resolved relative to themselves (no global stop on
+// the off-diagonal norm, a tighter pair threshold).
 template <typename R>
-lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st);
+lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st, int polish = 0);
 
 // FP64 small-matrix arithmetic of the sketches (small64.cu).
 // Gram matrices of complex64 blocks with error-free products (Dot2), FP64 result.
@@ -213,10 +215,11 @@ lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, do
 // FP64 Cholesky factor, s = shift_rel tr(G_b) / k (raised on breakdown).
 template <typename R>
 lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st);
-// Eigenvectors of the FP64 Hermitian G_b as the columns of V_b (k x k), by
-// decreasing eigenvalue: FP64 tridiagonalisation and implicit QL.
-template <typename R>
-lsw_status heev_ql(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st);
+// Eigenvectors of the FP64 Hermitian G_b as the columns of V_b (k x k, FP32),
+// by decreasing eigenvalue, resolved to FP64 accuracy: FP32 Jacobi, an
+// FP64-accurate Rayleigh-Ritz projection B = V0^H G V0, FP32 Jacobi on the
+// nearly diagonal B, V = V0 Z.
+lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t st);
 // Thin QR of complex64 sketch blocks (Q in place): shifted Cholesky QR3 with
 // FP64 Grams and factors, or FP64 Householder for short blocks.
 lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaStream_t st);

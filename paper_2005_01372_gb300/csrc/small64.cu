@@ -3,10 +3,11 @@
 // shifted Cholesky QR, and the Hermitian eigen-decomposition of the small
 // Gram matrix that truncates Q Yt^H to rank r.  The tall factors (Y, Q, Yt)
 // stay in the working precision; every k x k matrix derived from them
-// (k <= 64 columns) is formed and factored in FP64.
+// (k <= 64 columns) is formed and factored with FP64 accuracy.
 //
 // FP64 on this GPU runs at 1/62 of the FP32 rate (1.25 against 78 TFLOP/s,
-// measured), so the Gram of a complex64 block is accumulated with
+// measured) and its dependent chains are slow, so long serial FP64 code is
+// avoided: the Gram of a complex64 block is accumulated with
 // error-free transformations in FP32 arithmetic: every product a*b is split
 // exactly into p + e (p = fl(a b), e = fma(a, b, -p)) and summed with
 // TwoSum, which is Dot2 of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26,
@@ -120,110 +121,166 @@ __global__ void k_gram_c64_reduce(const double2* __restrict__ part, int nchunk, 
         const int j = ij / k, i = ij - j * k;
         const int lo = min(i, j), hi = max(i, j);
         const int p = hi * (hi + 1) / 2 + lo;
-        double2 s = make_double2(0.0, 0.0);
-        for (int c = 0; c < nchunk; ++c) {
-            const double2 v = part[((long long)b * nchunk + c) * npair + p];
-            s.x += v.x;
-            s.y += v.y;
+        // eight interleaved partial sums: short FP64 dependency chains
+        double2 acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = make_double2(0.0, 0.0);
+        const double2* src = part + (long long)b * nchunk * npair + p;
+        int c = 0;
+        for (; c + 8 <= nchunk; c += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const double2 v = src[(long long)(c + u) * npair];
+                acc[u].x += v.x;
+                acc[u].y += v.y;
+            }
         }
+        for (int u = 0; c < nchunk; ++c, ++u) {
+            const double2 v = src[(long long)c * npair];
+            acc[u].x += v.x;
+            acc[u].y += v.y;
+        }
+        double2 s = make_double2(((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x)) + ((acc[4].x + acc[5].x) + (acc[6].x + acc[7].x)),
+                                 ((acc[0].y + acc[1].y) + (acc[2].y + acc[3].y)) + ((acc[4].y + acc[5].y) + (acc[6].y + acc[7].y)));
         if (i > j) s.y = -s.y;   // G(i, j) = conj(G(j, i))
         G[e] = s;
     }
 }
 
 // ------------------------------------------- Cholesky and R^-1 (FP64)
-// One warp per matrix: G + shift I = L L^H (L = R^H lower triangular), then
-// X = L^-1 by forward substitution (each lane owns columns of X), and
-// Rinv = R^-1 = X^H.  A non-positive pivot restarts the factorisation with a
-// larger shift (1e-15 tr(G) / k, then x100, at most 12 times).  A block with
-// tr(G) = 0 gets Rinv = 0 (its Q is zero, which the truncation keeps as a
-// zero block).
+// One CTA per matrix: G + shift I = L L^H (L = R^H lower triangular), then
+// X = L^-1 and Rinv = R^-1 = X^H.  Written for the latency and rate of FP64
+// on this GPU: every pivot's reciprocal square root comes from an FP32
+// estimate and two Newton steps (no FP64 division or square root on the
+// chain), the trailing update and the substitution are independent
+// multiply-adds spread over four warps (the four FP64 units of an SM), and
+// the substitution runs in axpy form for all columns at once, so a step
+// waits on one multiply-add, not on a dot product.
+// A non-positive pivot restarts the factorisation with a larger shift
+// (1e-15 tr(G) / k, then x100, at most 12 times).  A block with tr(G) = 0
+// gets Rinv = 0 (its Q is zero, which the truncation keeps as a zero block).
+__device__ __forceinline__ double rsqrt64(double d) {
+    float f = (float)d;
+    double y = (f > 1e-37f && f < 1e37f) ? (double)rsqrtf(f) : 1.0 / sqrt(d);
+    // y <- y (3 - d y^2) / 2, twice: relative error ~1e-7 -> ~1e-14 -> rounding
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-d * y, y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y;
+}
+
 template <typename C>
 __global__ void __launch_bounds__(128)
 k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel, C* __restrict__ Rall) {
+    // one CTA (four warps, one per SM sub-partition and its FP64 unit) per matrix
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mat = blockIdx.x * (blockDim.x >> 5) + w;
-    if (mat >= batch) return;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int mat = blockIdx.x;
     const int ld = k + 1;
-    double2* L = reinterpret_cast<double2*>(sm_raw) + (size_t)w * 2 * k * ld;
+    double2* L = reinterpret_cast<double2*>(sm_raw);
     double2* X = L + (size_t)k * ld;
+    double* rinv = reinterpret_cast<double*>(X + (size_t)k * ld);
+    __shared__ double red[4];
+    __shared__ int fail;
     const double2* G = Gall + (long long)mat * k * k;
     C* Rout = Rall + (long long)mat * k * k;
     double tr = 0.0;
-    for (int i = 0; i < k; ++i) tr += G[i * k + i].x;
-    tr /= k;
+    for (int i = tid; i < k; i += NT) tr += G[i * k + i].x;
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if ((tid & 31) == 0) red[tid >> 5] = tr;
+    __syncthreads();
+    tr = (red[0] + red[1] + red[2] + red[3]) / k;
     if (!(tr > 0.0) || !isfinite(tr)) {
         const double fill = (tr == 0.0) ? 0.0 : NAN;
-        for (int e = lane; e < k * k; e += 32) { Rout[e].x = fill; Rout[e].y = fill; }
+        for (int e = tid; e < k * k; e += NT) { Rout[e].x = fill; Rout[e].y = fill; }
         return;
     }
     double shift = shift_rel * tr;
     bool ok = false;
     for (int attempt = 0; attempt < 13 && !ok; ++attempt) {
-        for (int e = lane; e < k * k; e += 32) {
+        for (int e = tid; e < k * k; e += NT) {
             const int j = e / k, i = e - j * k;
             double2 v = G[e];
             if (i == j) { v.x += shift; v.y = 0.0; }
             L[j * ld + i] = v;
         }
-        __syncwarp();
-        ok = true;
+        if (tid == 0) fail = 0;
+        __syncthreads();
         for (int j = 0; j < k; ++j) {
             const double djj = L[j * ld + j].x;
-            if (!(djj > 0.0) || !isfinite(djj)) { ok = false; break; }
-            const double rjj = sqrt(djj), irj = 1.0 / rjj;
-            __syncwarp();
-            for (int i = j + 1 + lane; i < k; i += 32) {
-                double2 v = L[j * ld + i];
-                L[j * ld + i] = make_double2(v.x * irj, v.y * irj);
+            if (!(djj > 0.0) || !isfinite(djj)) {    // uniform: every thread reads the same pivot
+                if (tid == 0) fail = 1;
+                break;
             }
-            if (lane == 0) L[j * ld + j] = make_double2(rjj, 0.0);
-            __syncwarp();
+            const double r = rsqrt64(djj);
+            __syncthreads();
+            for (int i = j + 1 + tid; i < k; i += NT) {
+                const double2 v = L[j * ld + i];
+                L[j * ld + i] = make_double2(v.x * r, v.y * r);
+            }
+            if (tid == 0) {
+                L[j * ld + j] = make_double2(djj * r, 0.0);
+                rinv[j] = r;
+            }
+            __syncthreads();
             // trailing lower triangle: L(i, l) -= L(i, j) conj(L(l, j)), j < l <= i
             const int nt = k - 1 - j;
-            for (int e = lane; e < nt * nt; e += 32) {
-                const int l = j + 1 + e / nt, i = j + 1 + e % nt;
-                if (i < l) continue;
+            for (int e = tid; e < nt * nt; e += NT) {
+                const int ll = e / nt, ii = e - ll * nt;
+                if (ii < ll) continue;
+                const int i = j + 1 + ii, l = j + 1 + ll;
                 const double2 a = L[j * ld + i], bq = L[j * ld + l];
                 double2 v = L[l * ld + i];
                 v.x -= a.x * bq.x + a.y * bq.y;
                 v.y -= a.y * bq.x - a.x * bq.y;
                 L[l * ld + i] = v;
             }
-            __syncwarp();
+            __syncthreads();
         }
-        __syncwarp();
+        __syncthreads();
+        ok = fail == 0;
+        __syncthreads();
         if (!ok) shift = shift > 0.0 ? shift * 100.0 : 1e-15 * tr;
     }
     if (!ok) {
-        for (int e = lane; e < k * k; e += 32) { Rout[e].x = NAN; Rout[e].y = NAN; }
+        for (int e = tid; e < k * k; e += NT) { Rout[e].x = NAN; Rout[e].y = NAN; }
         return;
     }
-    // X = L^-1 (lower): column c by forward substitution
-    for (int c = lane; c < k; c += 32) {
-        for (int i = 0; i < c; ++i) X[c * ld + i] = make_double2(0.0, 0.0);
-        X[c * ld + c] = make_double2(1.0 / L[c * ld + c].x, 0.0);
-        for (int i = c + 1; i < k; ++i) {
-            double sx = 0.0, sy = 0.0;
-            for (int t = c; t < i; ++t) {
-                const double2 a = L[t * ld + i], x = X[c * ld + t];
-                sx += a.x * x.x - a.y * x.y;
-                sy += a.x * x.y + a.y * x.x;
-            }
-            const double il = 1.0 / L[i * ld + i].x;
-            X[c * ld + i] = make_double2(-sx * il, -sy * il);
-        }
+    // X = L^-1 in axpy form, every column at once: X starts as I; step t
+    // fixes row t (x_t = b_t / L(t, t) in each column c <= t) and removes it
+    // from the rows below: b_i -= L(i, t) x_t.
+    for (int e = tid; e < k * ld; e += NT) {
+        const int c = e / ld, i = e - c * ld;
+        X[e] = make_double2(i == c ? 1.0 : 0.0, 0.0);
     }
-    __syncwarp();
+    __syncthreads();
+    for (int t = 0; t < k; ++t) {
+        const double rt = rinv[t];
+        for (int c = tid; c <= t; c += NT) {
+            const double2 bt = X[c * ld + t];
+            X[c * ld + t] = make_double2(bt.x * rt, bt.y * rt);
+        }
+        __syncthreads();
+        const int nr = k - 1 - t, nc = t + 1;
+        for (int e = tid; e < nr * nc; e += NT) {
+            const int c = e / nr, i = t + 1 + (e - c * nr);
+            const double2 a = L[t * ld + i], xt = X[c * ld + t];
+            double2 v = X[c * ld + i];
+            v.x -= a.x * xt.x - a.y * xt.y;
+            v.y -= a.x * xt.y + a.y * xt.x;
+            X[c * ld + i] = v;
+        }
+        __syncthreads();
+    }
     // Rinv(i, j) = conj(X(j, i)), upper triangular
-    for (int e = lane; e < k * k; e += 32) {
+    for (int e = tid; e < k * k; e += NT) {
         const int j = e / k, i = e - j * k;
         C v;
         if (i <= j) {
-            const double2 x = X[i * ld + j];
-            v.x = x.x;
-            v.y = -x.y;
+            const double2 xv = X[i * ld + j];
+            v.x = xv.x;
+            v.y = -xv.y;
         } else {
             v.x = 0;
             v.y = 0;
@@ -232,263 +289,77 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
     }
 }
 
-// ------------------------------------ Hermitian eigen-decomposition (FP64)
-// One warp per matrix (k <= 64).  (1) Householder reduction to a real
-// symmetric tridiagonal T = Q^H A Q, Q = H_0 ... H_{k-2}, each
-// H_j = I - tau_j v_j v_j^H chosen so that H_j^H maps the column below the
-// diagonal onto a real multiple of e_1 (the reflector convention of LAPACK's
-// zlarfg); the two-sided update is A <- A - v w^H - w v^H with p = tau A v,
-// w = p - (s / 2) v, s = conj(tau) v^H p (real).  (2) Implicit QL iteration
-// with Wilkinson shifts on T (Bowdler, Martin, Reinsch and Wilkinson, Numer.
-// Math. 11, 1968): lane 0 runs the scalar recurrence of one sweep and
-// records its plane rotations, then every lane applies them to its rows of
-// the eigenvector matrix.  (3) V = H_0 ... H_{k-2} Z, one column per lane.
-// Output: the eigenvectors as columns, by decreasing eigenvalue.  An
-// eigenvalue that needs more than 60 QL sweeps marks the result NaN.
-struct QlWarp {
-    double2* A;      // k x ld: the matrix, then the reflectors v_j below the diagonal
-    double2* V;      // k x ld: Z (real parts), then the eigenvectors
-    double* d;       // k
-    double* e;       // k
-    double* rc;      // 64: rotation cosines of one sweep
-    double* rs;      // 64: rotation sines
-    double2* tau;    // k
-    double2* wv;     // 64
-    int* order;      // 64
-};
-
-__host__ __device__ inline size_t ql_warp_bytes(int k) {
-    const size_t ld = (size_t)k + 1;
-    return sizeof(double2) * (2 * (size_t)k * ld + (size_t)k + 64) + sizeof(double) * (2 * (size_t)k + 128) +
-           sizeof(int) * 64 + 16;
-}
-
-template <typename C>
-__global__ void __launch_bounds__(64)
-k_heev_ql(const double2* __restrict__ Gall, C* __restrict__ Vall, int k, int batch) {
+// ------------------------------- Rayleigh-Ritz projection (FP64 accuracy)
+// B = V0^H G V0 for FP32 approximate eigenvectors V0 of the FP64 Hermitian G,
+// formed with FP64 accuracy in FP32 arithmetic: G = Ghi + Glo (two FP32
+// parts), W = G V0 by Dot2 over the Ghi terms with the Glo terms added to the
+// compensation, kept as the pair Whi + Wlo; then B = V0^H (Whi + Wlo) the
+// same way.  One CTA per matrix; B is written Hermitian (upper triangle
+// computed, lower mirrored).  Small eigenvalues of G that FP32 could not
+// separate inside G (below ~1e-7 of the largest) sit on B's diagonal with
+// their own exponents, where an FP32 Jacobi resolves them.
+__global__ void __launch_bounds__(128)
+k_rr_project(const double2* __restrict__ Gall, const float2* __restrict__ V0all, int k, double2* __restrict__ Ball) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mat = blockIdx.x * (blockDim.x >> 5) + w;
-    if (mat >= batch) return;
-    const int ld = k + 1;
-    const size_t per = (ql_warp_bytes(k) + 15) & ~size_t(15);
-    unsigned char* base = sm_raw + (size_t)w * per;
-    QlWarp s;
-    s.A = reinterpret_cast<double2*>(base);
-    s.V = s.A + (size_t)k * ld;
-    s.tau = s.V + (size_t)k * ld;
-    s.wv = s.tau + k;
-    s.d = reinterpret_cast<double*>(s.wv + 64);
-    s.e = s.d + k;
-    s.rc = s.e + k;
-    s.rs = s.rc + 64;
-    s.order = reinterpret_cast<int*>(s.rs + 64);
-    const double2* G = Gall + (long long)mat * k * k;
-    for (int q = lane; q < k * k; q += 32) {
-        const int j = q / k, i = q - j * k;
-        s.A[j * ld + i] = G[q];
-        s.V[j * ld + i] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    const int kk = k * k;
+    float2* Ghi = reinterpret_cast<float2*>(sm_raw);
+    float2* Glo = Ghi + kk;
+    float2* V = Glo + kk;
+    float2* Whi = V + kk;
+    float2* Wlo = Whi + kk;
+    const double2* G = Gall + (long long)blockIdx.x * kk;
+    const float2* V0 = V0all + (long long)blockIdx.x * kk;
+    double2* B = Ball + (long long)blockIdx.x * kk;
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        const double2 g = G[e];
+        const float hx = (float)g.x, hy = (float)g.y;
+        Ghi[e] = make_float2(hx, hy);
+        Glo[e] = make_float2((float)(g.x - (double)hx), (float)(g.y - (double)hy));
+        V[e] = V0[e];
     }
-    __syncwarp();
-    // (1) tridiagonalisation
-    for (int j = 0; j + 1 < k; ++j) {
-        const int m = k - 1 - j;                      // rows j+1 .. k-1
-        double2* x = s.A + j * ld + j + 1;            // column j below the diagonal
-        double part = 0.0;
-        for (int i = 1 + lane; i < m; i += 32) part += x[i].x * x[i].x + x[i].y * x[i].y;
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        const double2 alpha = x[0];
-        double2 t = make_double2(0.0, 0.0);
-        double beta = alpha.x;
-        if (part > 0.0 || alpha.y != 0.0) {
-            const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + part);
-            beta = alpha.x >= 0.0 ? -nrm : nrm;
-            t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-            // v = [1; x[1:] / (alpha - beta)]
-            const double dr = alpha.x - beta, di = alpha.y;
-            const double den = dr * dr + di * di;
-            const double ir = dr / den, ii = -di / den;
-            __syncwarp();
-            for (int i = 1 + lane; i < m; i += 32) {
-                const double2 v = x[i];
-                x[i] = make_double2(v.x * ir - v.y * ii, v.x * ii + v.y * ir);
-            }
-            if (lane == 0) x[0] = make_double2(1.0, 0.0);
-            __syncwarp();
-            // p = tau A22 v, rows lane and lane + 32 (m <= 63)
-            double2 p[2];
-            for (int u = 0; u < 2; ++u) {
-                const int i = lane + 32 * u;
-                double sx = 0.0, sy = 0.0;
-                if (i < m) {
-                    for (int l = 0; l < m; ++l) {
-                        const double2 a = s.A[(j + 1 + l) * ld + j + 1 + i], v = x[l];
-                        sx += a.x * v.x - a.y * v.y;
-                        sy += a.x * v.y + a.y * v.x;
-                    }
-                }
-                p[u] = make_double2(t.x * sx - t.y * sy, t.x * sy + t.y * sx);
-            }
-            // c = v^H p, s = Re(conj(tau) c)
-            double cx = 0.0, cy = 0.0;
-            for (int u = 0; u < 2; ++u) {
-                const int i = lane + 32 * u;
-                if (i < m) {
-                    const double2 v = x[i];
-                    cx += v.x * p[u].x + v.y * p[u].y;
-                    cy += v.x * p[u].y - v.y * p[u].x;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                cx += __shfl_xor_sync(0xffffffffu, cx, o);
-                cy += __shfl_xor_sync(0xffffffffu, cy, o);
-            }
-            const double sr = t.x * cx + t.y * cy;
-            for (int u = 0; u < 2; ++u) {
-                const int i = lane + 32 * u;
-                if (i < m) {
-                    const double2 v = x[i];
-                    s.wv[i] = make_double2(p[u].x - 0.5 * sr * v.x, p[u].y - 0.5 * sr * v.y);
-                }
-            }
-            __syncwarp();
-            // A22 -= v w^H + w v^H
-            for (int q = lane; q < m * m; q += 32) {
-                const int l = q / m, i = q - l * m;
-                const double2 vi = x[i], vl = x[l], wi = s.wv[i], wl = s.wv[l];
-                double2 a = s.A[(j + 1 + l) * ld + j + 1 + i];
-                a.x -= vi.x * wl.x + vi.y * wl.y + wi.x * vl.x + wi.y * vl.y;
-                a.y -= vi.y * wl.x - vi.x * wl.y + wi.y * vl.x - wi.x * vl.y;
-                s.A[(j + 1 + l) * ld + j + 1 + i] = a;
-            }
-            __syncwarp();
+    __syncthreads();
+    // W(i, j) = sum_t G(i, t) V(t, j)
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        const int j = e / k, i = e - j * k;
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        for (int t = 0; t < k; ++t) {
+            const float2 gh = Ghi[t * k + i], gl = Glo[t * k + i], v = V[j * k + t];
+            dot2(gh.x, v.x, sr, cr);
+            dot2(-gh.y, v.y, sr, cr);
+            dot2(gh.x, v.y, si, ci);
+            dot2(gh.y, v.x, si, ci);
+            cr = fmaf(gl.x, v.x, fmaf(-gl.y, v.y, cr));
+            ci = fmaf(gl.x, v.y, fmaf(gl.y, v.x, ci));
         }
-        if (lane == 0) {
-            s.tau[j] = t;
-            s.e[j] = beta;
-            s.d[j] = s.A[j * ld + j].x;
+        // renormalise the pair so that Whi carries the leading bits
+        const float hr = __fadd_rn(sr, cr), hi = __fadd_rn(si, ci);
+        Whi[e] = make_float2(hr, hi);
+        Wlo[e] = make_float2(__fsub_rn(cr, __fsub_rn(hr, sr)), __fsub_rn(ci, __fsub_rn(hi, si)));
+    }
+    __syncthreads();
+    // B(i, j) = sum_t conj(V(t, i)) W(t, j), i <= j
+    const int npair = k * (k + 1) / 2;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+        int i, j;
+        tri_pair(p, i, j);
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        for (int t = 0; t < k; ++t) {
+            const float2 a = V[i * k + t], wh = Whi[j * k + t], wl = Wlo[j * k + t];
+            // conj(a) * w = (ax wx + ay wy) + i (ax wy - ay wx)
+            dot2(a.x, wh.x, sr, cr);
+            dot2(a.y, wh.y, sr, cr);
+            dot2(a.x, wh.y, si, ci);
+            dot2(-a.y, wh.x, si, ci);
+            cr = fmaf(a.x, wl.x, fmaf(a.y, wl.y, cr));
+            ci = fmaf(a.x, wl.y, fmaf(-a.y, wl.x, ci));
         }
-        __syncwarp();
-    }
-    if (lane == 0) {
-        s.d[k - 1] = s.A[(k - 1) * ld + k - 1].x;
-        s.e[k - 1] = 0.0;
-        s.tau[k - 1] = make_double2(0.0, 0.0);
-    }
-    __syncwarp();
-    // (2) implicit QL
-    int failed = 0;
-    for (int l = 0; l < k && !failed; ++l) {
-        for (int iter = 0;; ++iter) {
-            // lane 0: one sweep; code: 0 converged, 1 rotations in rc/rs for
-            // i = m-1 down to lo, 2 failed
-            int code = 0, mm = l, lo = l;
-            if (lane == 0) {
-                double* d = s.d;
-                double* e = s.e;
-                int m = l;
-                for (; m < k - 1; ++m) {
-                    const double dd = fabs(d[m]) + fabs(d[m + 1]);
-                    if (fabs(e[m]) <= DBL_EPSILON * dd) break;
-                }
-                mm = m;
-                if (m == l) code = 0;
-                else if (iter == 60) code = 2;
-                else {
-                    code = 1;
-                    double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-                    double r = hypot(g, 1.0);
-                    g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-                    double sn = 1.0, cs = 1.0, p = 0.0;
-                    int i = m - 1;
-                    bool under = false;
-                    for (; i >= l; --i) {
-                        const double f = sn * e[i], b = cs * e[i];
-                        r = hypot(f, g);
-                        e[i + 1] = r;
-                        if (r == 0.0) {
-                            d[i + 1] -= p;
-                            e[m] = 0.0;
-                            under = true;
-                            break;
-                        }
-                        sn = f / r;
-                        cs = g / r;
-                        g = d[i + 1] - p;
-                        r = (d[i] - g) * sn + 2.0 * cs * b;
-                        p = sn * r;
-                        d[i + 1] = g + p;
-                        g = cs * r - b;
-                        s.rc[i] = cs;
-                        s.rs[i] = sn;
-                    }
-                    lo = under ? i + 1 : l;
-                    if (!under) {
-                        d[l] -= p;
-                        e[l] = g;
-                        e[m] = 0.0;
-                    }
-                }
-            }
-            code = __shfl_sync(0xffffffffu, code, 0);
-            mm = __shfl_sync(0xffffffffu, mm, 0);
-            lo = __shfl_sync(0xffffffffu, lo, 0);
-            __syncwarp();
-            if (code == 0) break;
-            if (code == 2) { failed = 1; break; }
-            for (int i = mm - 1; i >= lo; --i) {
-                const double cs = s.rc[i], sn = s.rs[i];
-                for (int row = lane; row < k; row += 32) {
-                    const double zf = s.V[(i + 1) * ld + row].x, zi = s.V[i * ld + row].x;
-                    s.V[(i + 1) * ld + row].x = sn * zi + cs * zf;
-                    s.V[i * ld + row].x = cs * zi - sn * zf;
-                }
-            }
-            __syncwarp();
+        const double br = (double)sr + (double)cr, bi = (double)si + (double)ci;
+        if (i == j) {
+            B[j * k + i] = make_double2(br, 0.0);
+        } else {
+            B[j * k + i] = make_double2(br, bi);
+            B[i * k + j] = make_double2(br, -bi);
         }
-    }
-    __syncwarp();
-    // (3) V = H_0 ... H_{k-2} Z, column by column
-    for (int col = lane; col < k; col += 32) {
-        double2* vc = s.V + col * ld;
-        for (int j = k - 2; j >= 0; --j) {
-            const double2 t = s.tau[j];
-            if (t.x == 0.0 && t.y == 0.0) continue;
-            const double2* v = s.A + j * ld + j + 1;    // rows j+1 .. k-1, v[0] = 1
-            double sx = 0.0, sy = 0.0;
-            for (int i = j + 1; i < k; ++i) {
-                const double2 vv = v[i - j - 1], x = vc[i];
-                sx += vv.x * x.x + vv.y * x.y;
-                sy += vv.x * x.y - vv.y * x.x;
-            }
-            const double tx = t.x * sx - t.y * sy, ty = t.x * sy + t.y * sx;
-            for (int i = j + 1; i < k; ++i) {
-                const double2 vv = v[i - j - 1];
-                vc[i].x -= vv.x * tx - vv.y * ty;
-                vc[i].y -= vv.x * ty + vv.y * tx;
-            }
-        }
-    }
-    if (lane == 0) {
-        for (int i = 0; i < k; ++i) s.order[i] = i;
-        for (int i = 0; i < k; ++i) {
-            int best = i;
-            for (int jj = i + 1; jj < k; ++jj)
-                if (s.d[s.order[jj]] > s.d[s.order[best]]) best = jj;
-            const int tmp = s.order[i];
-            s.order[i] = s.order[best];
-            s.order[best] = tmp;
-        }
-    }
-    __syncwarp();
-    C* Vo = Vall + (long long)mat * k * k;
-    for (int q = lane; q < k * k; q += 32) {
-        const int col = q / k, row = q - col * k;
-        const double2 v = s.V[s.order[col] * ld + row];
-        C o;
-        o.x = failed ? NAN : v.x;
-        o.y = failed ? NAN : v.y;
-        Vo[q] = o;
     }
 }
 
@@ -517,6 +388,7 @@ lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, do
     const int npair = k * (k + 1) / 2;
     DevBuf part;
     LSW_TRY(part.alloc(sizeof(double2) * (size_t)batch * nchunk * npair, st));
+    KTimer kt("gram", st, 8.0 * batch * (double)m * k, 0.0);
     k_gram_c64<<<dim3(nchunk, batch), 256, sizeof(float2) * (GT_ROWS + 1) * k, st>>>(Y, m, k, sY, nchunk,
                                                                                         part.as<double2>());
     LSW_LAUNCH_CHECK();
@@ -530,33 +402,39 @@ lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typen
     typedef typename Cx<R>::T C;
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
-    const size_t per = sizeof(double2) * 2 * (size_t)k * (k + 1);
-    const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (160 * 1024) / per));
+    const size_t per = sizeof(double2) * (2 * (size_t)k * (k + 1) + k);
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         LSW_CUDA(cudaFuncSetAttribute(k_chol_rinv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr.store(true);
     }
-    k_chol_rinv<C><<<(batch + wpc - 1) / wpc, 32 * wpc, per * wpc, st>>>(G, k, batch, shift_rel, Rinv);
+    KTimer kt("chol", st, 0.0, 0.0);
+    k_chol_rinv<C><<<batch, 128, per, st>>>(G, k, batch, shift_rel, Rinv);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
 
-template <typename R>
-lsw_status heev_ql(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st) {
-    typedef typename Cx<R>::T C;
+lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t st) {
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
-    const size_t perA = (ql_warp_bytes(k) + 15) & ~size_t(15);
-    const int wpc = (int)std::max<size_t>(1, std::min<size_t>(2, (200 * 1024) / perA));
+    KTimer kt("heev", st, 0.0, 0.0);
+    const size_t kk = (size_t)k * k;
+    DevBuf V0, B, Z;
+    LSW_TRY(V0.alloc(sizeof(float2) * kk * batch, st));
+    LSW_TRY(B.alloc(sizeof(double2) * kk * batch, st));
+    LSW_TRY(Z.alloc(sizeof(float2) * kk * batch, st));
+    LSW_TRY(heev_jacobi<float>(G, V0.as<float2>(), k, batch, st, 0));
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
-        LSW_CUDA(cudaFuncSetAttribute(k_heev_ql<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
+        LSW_CUDA(cudaFuncSetAttribute(k_rr_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr.store(true);
     }
-    k_heev_ql<C><<<(batch + wpc - 1) / wpc, 32 * wpc, perA * wpc, st>>>(G, V, k, batch);
+    k_rr_project<<<batch, 128, sizeof(float2) * 5 * kk, st>>>(G, V0.as<float2>(), k, B.as<double2>());
     LSW_LAUNCH_CHECK();
-    return LSW_OK;
+    LSW_TRY(heev_jacobi<float>(B.as<double2>(), Z.as<float2>(), k, batch, st, 1));
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    return gemm<float>('N', 'N', k, k, k, one, V0.as<float2>(), k, (long long)kk, Z.as<float2>(), k, (long long)kk,
+                       zero, V, k, (long long)kk, batch, st);
 }
 
 // Thin QR of complex64 sketch blocks, Q returned in place of A (m x k, ld m,
@@ -601,7 +479,5 @@ lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaS
 
 template lsw_status chol_rinv<float>(const double2*, int, int, double, float2*, cudaStream_t);
 template lsw_status chol_rinv<double>(const double2*, int, int, double, double2*, cudaStream_t);
-template lsw_status heev_ql<float>(const double2*, float2*, int, int, cudaStream_t);
-template lsw_status heev_ql<double>(const double2*, double2*, int, int, cudaStream_t);
 
 }  // namespace lsw
