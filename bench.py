@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """Benchmark: Lippmann-Schwinger solves per second on one GB300.
 
-Workload (one "step" = one pass of the whole method over one batch):
-  256 x 256 grid, h = 10 m, c0 = 2000 m/s, f = 15 Hz, seeded random layered
-  medium (8-20 dipping layers, 1500-4500 m/s) with a 4500 m/s salt-like
-  ellipse; 32 point sources along the top row.  The step builds the Green
-  table and spectrum, the contrast and the source fields, the randomized
-  HODLR preconditioner (quadtree 32 x 32 leaves, 6 levels, rank 20 + 10
-  Gaussian probes, q = 0) in FP32 with its recursive block inversion, and
-  solves all 32 sources to an FP64 relative residual of 1e-6: FP32 FGMRES(30)
-  with H as right preconditioner inside FP64 iterative refinement.  Only
-  sources that reach 1e-6 count as solves.
+Workload (one "step" = one pass of the whole method over one batch): the
+largest configuration that fits one GPU, a 1024 x 1024 grid (h = 5 m,
+c0 = 2000 m/s, f = 30 Hz) with a seeded Marmousi-like velocity model
+(30-60 smoothed layers, 1500-5500 m/s with depth, 5-10 faults) and 16 point
+sources on the top row.  The step builds the Green table and spectrum, the
+contrast and the source fields, the randomized HODLR preconditioner
+(quadtree 32 x 32 leaves, 10 levels, rank 40 + 10 Gaussian probes, q = 0;
+built in FP32 with FP64-accurate sketch QR and truncation, kept as BF16)
+with its recursive block inversion, and solves all 16 sources to an FP64
+relative residual of 1e-6: FP32 FGMRES(30) with H as right preconditioner
+inside FP64 iterative refinement.  Only sources that reach 1e-6 count as
+solves.
 
 Multi-GPU (torchrun): every rank solves its own copy of the workload
 (independent (source, frequency) problems, no data-path collective); value is
@@ -34,8 +36,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LS solves/sec (src x freq) at rel. residual 1e-6; FFT-operator HBM GB/s vs peak"
-WORKLOAD = "layered-salt-256x256-15Hz-32src"
+WORKLOAD = "marmousi-like-1024x1024-30Hz-16src"
 TOL = 1e-6
+RANK, OVERSAMPLE, LEVELS, SEED = 40, 10, 10, 1004
 
 
 def load_peaks():
@@ -102,16 +105,25 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-DOMINANT = "qr"
-# DRAM bytes (read + write) per k_tsqr_chunk launch, from one ncu capture of all
-# 251 launches of the benchmark's HODLR build (profiles/qr_chunk_hodlr_build_256x256.md)
-QR_TRAFFIC_PER_LAUNCH = 1575836
+# The kernel family with the largest share of the step's launch list (see
+# profiles/), timed live with CUDA events on its launching stream.
+DOMINANT = "heev"
+DOMINANT_KERNEL = ("heev: FP64-accurate eigen-decomposition of the sketches' Gram matrices (FP32 Jacobi, "
+                   "FP64-accurate Rayleigh-Ritz projection, FP32 Jacobi on the projection)")
+# DRAM bytes (read + write) per launch of the dominant family from one ncu
+# capture of this workload's step, or None when not captured for this build.
+DOMINANT_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes of one 16-field 1024^2 FP32 RESIDUAL apply (passes k_fa, k_fb,
+# k_fc), from one ncu capture (profiles/fft_operator_passes_1024x1024_c64.md).
+OPERATOR_TRAFFIC = None
 
 
-def fp32_alu_peak_tflops() -> float:
-    """FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops
-    (fused multiply-add) x 2.07 GHz maximum SM clock."""
-    return round(152 * 128 * 2 * 2.07e9 / 1e12, 1)
+def fp32_alu_peak_tflops(sms: int = 152, sm_mhz: float = 2070.0) -> float:
+    """Nominal FP32 CUDA-core peak from the SM count and the maximum SM
+    clock: SMs x 128 FP32 lanes x 2 flops (fused multiply-add) x clock.
+    Only a fallback: the bench divides by the peak that lsw_measure_peak
+    measures on the device."""
+    return round(sms * 128 * 2 * sm_mhz * 1e6 / 1e12, 1)
 
 
 def op_bytes_c64(n: int, nsrc: int) -> float:
@@ -136,6 +148,16 @@ def reduce_over_ranks(ms_local: float, solves_local: float, device):
     return float(t.item()), float(c.item())
 
 
+def hparams(lsw):
+    return lsw.HParams(kind=lsw.H_HODLR, prec=lsw.BF16, levels=LEVELS, split=lsw.SPLIT_QUADTREE, rank=RANK,
+                       oversample=OVERSAMPLE, q=0, seed=SEED)
+
+
+def sparams(lsw):
+    return lsw.SolveParams(prec=lsw.MIXED, method=lsw.FGMRES, tol=TOL, inner_tol=1e-3, restart=30, max_iter=400,
+                           max_outer=8)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -151,13 +173,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    wl = media.layered_salt(256, 15.0, 32, 2)
+    wl = media.marmousi_1024()
     vel_host = torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).pin_memory()
     vel = vel_host.to(dev)
-    hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=6, split=lsw.SPLIT_QUADTREE, rank=20,
-                     oversample=10, q=0, seed=1002)
-    sp = lsw.SolveParams(prec=lsw.MIXED, method=lsw.FGMRES, tol=TOL, inner_tol=1e-3, restart=30, max_iter=60,
-                         max_outer=8)
+    hp, sp = hparams(lsw), sparams(lsw)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     def step(v):
@@ -173,9 +192,6 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, inputs resident in HBM, L2 flushed between steps.
-    # The dominant kernel family (the row-chunk QR of the sketch blocks, by its
-    # share of the ncu launch list) is timed live with CUDA events on its
-    # launching stream.
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -183,7 +199,7 @@ def run_ours(args):
     clocks.start()
     l0 = lsw.launch_count()
     lsw.kernel_timer_start(DOMINANT)
-    times, conv, worst = [], 0, 0.0
+    times, conv, worst, applies = [], 0, 0.0, []
     t_wall = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
@@ -196,6 +212,9 @@ def run_ours(args):
         ok = [i for i in infos if i.status == 0 and i.rel_residual <= TOL]
         conv += len(ok)
         worst = max(worst, max(i.rel_residual for i in infos))
+        # operator applies per source: one per inner iteration, one FP64
+        # residual per refinement step plus the initial one
+        applies.extend(i.iterations + i.outer + 1 for i in infos)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     launches = lsw.launch_count() - l0
@@ -210,7 +229,7 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers
     e2e_times = []
     out_host = torch.empty((len(wl.sources), wl.n), dtype=torch.complex128).pin_memory()
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(1):
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -225,9 +244,9 @@ def run_ours(args):
         float(np.mean(e2e_times)) / 1e3)
 
     # ---- the FFT operator alone (its three passes timed with CUDA events on
-    # its stream): the step's RESIDUAL apply in FP32 on the 32 source fields,
-    # with L2 flushed between applies (inside the solves most operator applies
-    # are replayed from a CUDA graph, which the family timer does not see)
+    # its stream): the solve's RESIDUAL apply in FP32 on the 16 source
+    # fields, with L2 flushed between applies (inside the solves most operator
+    # applies are replayed from a CUDA graph, which the family timer does not see)
     G = lsw.build_green(wl.nz, wl.nx, wl.h, wl.c0, wl.freq_hz)
     chi = G.contrast(vel)
     uf = G.point_sources(wl.sources, lsw.C64)
@@ -240,43 +259,51 @@ def run_ours(args):
         lsw.apply_operator(G, chi, uf, uf, lsw.OP_RESIDUAL, y=yf)
     op_ms, op_bytes, op_flops, op_n = lsw.kernel_timer_read()
     lsw.kernel_timer_stop()
+    fp32_peak = lsw.measure_peak(0)
 
     peak, peak_kind = load_peaks()
-    fp32_peak = fp32_alu_peak_tflops()
     dom_gbs = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    roof = {"kernel": "k_tsqr_chunk: row-chunk Householder QR of the sketch blocks (largest share of the "
-                      "step in the committed launch list)",
-            "bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": round(dom_gbs / peak, 4), "traffic": QR_TRAFFIC_PER_LAUNCH, "launches": int(dom_n),
-            "avg_launch_ms": round(dom_ms / max(1, dom_n), 4),
-            "achieved_tflops": round(dom_flops / (dom_ms / 1e3) / 1e12, 3) if dom_ms > 0 else 0.0}
+    dom_tf = dom_flops / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
+    roof = {"kernel": DOMINANT_KERNEL, "bound": "alu", "achieved": round(dom_tf, 4), "peak": round(fp32_peak, 2),
+            "peak_kind": "measured: lsw_measure_peak FP32 FMA probe on this device", "unit": "TFLOP/s",
+            "frac": round(dom_tf / fp32_peak, 5) if fp32_peak > 0 else None, "traffic": DOMINANT_TRAFFIC_PER_LAUNCH,
+            "launches": int(dom_n), "avg_launch_ms": round(dom_ms / max(1, dom_n), 4),
+            "achieved_gbs": round(dom_gbs, 2), "hbm_frac": round(dom_gbs / peak, 6)}
     op_tf = op_flops / (op_ms / 1e3) / 1e12 if op_ms > 0 else 0.0
     op_gbs = op_bytes / (op_ms / 1e3) / 1e9 if op_ms > 0 else 0.0
-    op_roof = {"kernel": "FFT operator in FP32, passes k_fa + k_fb + k_fc, RESIDUAL on the 32 source fields, "
-                         "timed alone with L2 flushed between applies", "bound": "alu",
-               "achieved": round(op_tf, 2), "peak": fp32_peak,
-               "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
-               "unit": "TFLOP/s", "frac": round(op_tf / fp32_peak, 4), "algorithmic_gbs": round(op_gbs, 1),
-               "hbm_frac": round(op_gbs / peak, 4), "applies": int(op_n),
-               "avg_apply_ms": round(op_ms / max(1, op_n), 4)}
+    op_avg = op_ms / max(1, op_n)
+    op_roof = {"kernel": "FFT operator in FP32, passes k_fa + k_fb + k_fc, RESIDUAL on the 16 source fields at "
+                         "1024^2, timed alone with L2 flushed between applies", "bound": "alu",
+               "achieved": round(op_tf, 2), "peak": round(fp32_peak, 2),
+               "peak_kind": "measured: lsw_measure_peak FP32 FMA probe on this device",
+               "unit": "TFLOP/s", "frac": round(op_tf / fp32_peak, 4) if fp32_peak > 0 else None,
+               "algorithmic_gbs": round(op_gbs, 1), "hbm_frac": round(op_gbs / peak, 4),
+               "hbm_peak": peak, "hbm_peak_kind": peak_kind,
+               "dram_traffic_per_apply": OPERATOR_TRAFFIC,
+               "dram_gbs": round(OPERATOR_TRAFFIC / (op_avg / 1e3) / 1e9, 1) if OPERATOR_TRAFFIC else None,
+               "dram_frac": round(OPERATOR_TRAFFIC / (op_avg / 1e3) / 1e9 / peak, 4) if OPERATOR_TRAFFIC else None,
+               "applies": int(op_n), "avg_apply_ms": round(op_avg, 4)}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+bf16+f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "grid": "256x256", "h_m": 10.0, "freq_hz": 15.0,
+                "config": {"workload": WORKLOAD, "grid": "1024x1024", "h_m": wl.h, "freq_hz": wl.freq_hz,
                            "sources_per_gpu": len(wl.sources),
-                           "preconditioner": "HODLR quadtree 32x32 leaves, 6 levels, rank 20+10, q=0, FP32",
+                           "preconditioner": f"HODLR quadtree 32x32 leaves, {LEVELS} levels, rank {RANK}+"
+                                             f"{OVERSAMPLE}, q=0, FP32 build, BF16 storage",
                            "solver": "FGMRES(30) right-preconditioned, FP64 iterative refinement to 1e-6",
                            "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas{world}"},
                 "solves_converged": int(solves), "max_rel_residual": worst,
+                "operator_applies_per_solve": round(float(np.mean(applies)), 1),
                 "roofline": roof, "operator_roofline": op_roof,
-                "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": int(vel_host.numel() * 8),
+                "e2e": {"value": round(e2e_value, 4), "unit": "solves/s",
+                        "h2d_bytes_per_step": int(vel_host.numel() * 8),
                         "d2h_bytes_per_step": int(out_host.numel() * 16)},
                 "clocks": clk, "gpu_launches": int(launches), "wall_s": round(wall, 3)}
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(float(np.mean(applies)))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -291,9 +318,10 @@ def run_extra(args):
       32 x 32 leaves, rank 20 + 10, FP32; FP32 FGMRES(30) in FP64 refinement
       to 1e-6), four problems at a time; --rank-max R lets a problem that
       does not converge be rebuilt with a doubled rank, up to R.
-    marmousi-1024: a 1024^2 Marmousi-like medium (h = 5 m, 30 Hz, 16 sources),
-      HODLR with 32 x 32 leaves (10 levels), rank 20 + 10, FP32, mixed-precision
-      FGMRES to 1e-6 (--rank-max as above).
+    layered-salt-256: a 256^2 layered medium with a salt ellipse (h = 10 m,
+      15 Hz, 32 sources on the top row), HODLR with 32 x 32 leaves (6 levels),
+      rank 20 + 10, FP32, mixed-precision FGMRES(30) to 1e-6; the build is in
+      every step.
     marmousi-subset-sweep / salt-subset-sweep: the paper's own experiment
       shapes (Sec. 3.1, 3.2): a 248 x 81 Marmousi-like model at h = 15 m
       embedded in a 256 x 128 grid, or a 700 x 150 salt model at h = 10 m
@@ -304,7 +332,7 @@ def run_extra(args):
       +10 after a failure within 30 iterations or a solve that needed more
       than 10, at most 50), and the paper's preconditioned series in FP32
       inside FP64 refinement to 1e-6 (--sweep-method fgmres: FGMRES(30)).
-    c128-one-at-a-time: the headline 256^2 salt workload on the plain FP64
+    c128-one-at-a-time: the 256^2 salt workload on the plain FP64
       path, one source per solve call: c128 operator, HODLR in FP64, FGMRES(30)
       in FP64; the build is charged once per 32 sources."""
     import torch
@@ -342,24 +370,25 @@ def run_extra(args):
                "preconditioner": f"HODLR 32x32 leaves, rank 20+10, FP32, rank raised up to {args.rank_max}"
                if args.rank_max > 20 else "HODLR 32x32 leaves, rank 20+10, FP32",
                "solver": "FGMRES(30) in FP64 refinement to 1e-6, lsw_solve_batched, 4 concurrent"}
-    elif args.workload == "marmousi-1024":
-        wl = media.marmousi_1024()
+    elif args.workload == "layered-salt-256":
+        wl = media.layered_salt(256, 15.0, 32, 2)
         vel = torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).to(dev)
-        hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=10, rank=20, oversample=10, seed=1004,
-                         rank_max=args.rank_max)
-        sp = lsw.SolveParams(prec=lsw.MIXED, method=lsw.FGMRES, tol=TOL, inner_tol=1e-3, restart=30, max_iter=120,
+        hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=6, split=lsw.SPLIT_QUADTREE, rank=20,
+                         oversample=10, q=0, seed=1002)
+        sp = lsw.SolveParams(prec=lsw.MIXED, method=lsw.FGMRES, tol=TOL, inner_tol=1e-3, restart=30, max_iter=60,
                              max_outer=8)
-        prob = {"nz": wl.nz, "nx": wl.nx, "h": wl.h, "c0": wl.c0, "freq_hz": wl.freq_hz, "sources": wl.sources,
-                "velocity": vel}
 
         def step():
-            _, infos = lsw.solve_batched([prob], hp, sp, max_concurrent=1)
-            ok = sum(1 for i in infos[0] if i.status == 0 and i.rel_residual <= TOL)
-            return ok, len(infos[0]), [ok]
-        cfg = {"workload": wl.name, "grid": "1024x1024", "h_m": wl.h, "freq_hz": wl.freq_hz,
-               "preconditioner": "HODLR 32x32 leaves, 10 levels, rank 20+10, FP32"
-               + (f", rank raised up to {args.rank_max}" if args.rank_max > 20 else ""),
-               "solver": "FGMRES(30) in FP64 refinement to 1e-6"}
+            G = lsw.build_green(wl.nz, wl.nx, wl.h, wl.c0, wl.freq_hz)
+            chi = G.contrast(vel)
+            u0 = G.point_sources(wl.sources, lsw.C128)
+            H = lsw.build_hmatrix(G, chi, hp)
+            _, infos = lsw.solve_series(G, chi, H, u0, sp=sp)
+            ok = sum(1 for i in infos if i.status == 0 and i.rel_residual <= TOL)
+            return ok, len(infos), None
+        cfg = {"workload": "layered-salt-256x256-15Hz-32src", "grid": "256x256", "h_m": 10.0, "freq_hz": 15.0,
+               "preconditioner": "HODLR quadtree 32x32 leaves, 6 levels, rank 20+10, q=0, FP32",
+               "solver": "FGMRES(30) right-preconditioned, FP64 iterative refinement to 1e-6"}
     elif args.workload in ("marmousi-subset-sweep", "salt-subset-sweep"):
         wl = media.marmousi_subset() if args.workload.startswith("marmousi") else media.salt_subset()
         vel = torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).to(dev)
@@ -398,7 +427,8 @@ def run_extra(args):
                 _, inf = lsw.solve_series(G, chi, H, u0, sp=sp)
                 ok += sum(1 for i in inf if i.status == 0 and i.rel_residual <= TOL)
             return ok, len(wl.sources), None
-        cfg = {"workload": WORKLOAD, "path": "c128 operator, FP64 HODLR, FP64 FGMRES(30), one source per call"}
+        cfg = {"workload": "layered-salt-256x256-15Hz-32src",
+               "path": "c128 operator, FP64 HODLR, FP64 FGMRES(30), one source per call"}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -421,55 +451,60 @@ def run_extra(args):
     print(json.dumps(line), flush=True)
 
 
-class OracleArm:
-    """The CPU oracle, as it stands, on the same workload.
+# Operator applies per solve of the headline workload on the GPU path (inner
+# FGMRES iterations + FP64 residuals, mean over the 16 sources), measured by
+# this bench on GB300 ("operator_applies_per_solve" of its line).  The
+# reference arm, which runs without a GPU, converts its per-apply time to
+# solves/s with it.
+APPLIES_PER_SOLVE = 300.0
 
-    One oracle "step" is one complete solve: FGMRES(30) for one source to an
-    FP64 relative residual of 1e-6, right-preconditioned by the oracle's own
-    randomized HODLR (same tree, rank, probes).  The preconditioner is shared
-    by the 32 sources of the workload, exactly as on the GPU, so it is built
-    once per arm (Green spectrum, contrast, sources, HODLR build and
-    inversion, timed) and one thirty-second of that time is charged to every
-    step.  solves/s = 1 / (t_build / 32 + t_solve)."""
+
+class OracleArm:
+    """The CPU oracle, as it stands, on a bounded sample of the workload.
+
+    A complete oracle solve of the 1024^2 workload is out of reach: its
+    HODLR preconditioner has 1024 dense leaves of 1024 x 1024 (16 GB in
+    complex128) and a recursive inversion of hours.  What the oracle can do
+    in bounded time is the part every solve repeats most: one FP64
+    application of I - G0 V (RESIDUAL mode, the FFT convolution on the
+    zero-padded 2048 x 2048 grid) for one source.  A step times one such
+    apply; solves/s = 1 / (applies per solve x seconds per apply), with the
+    GPU path's measured applies per solve.  Leaving out the preconditioner's
+    build and apply makes this an upper bound on the oracle's solves/s."""
 
     def __init__(self):
-        from oracle import hodlr as oh
         from oracle import operator as oop
-        from oracle import solve as osolve
         from paper_2005_01372_gb300 import media
 
-        self.osolve = osolve
-        self.oh = oh
+        self.oop = oop
         self.cores = len(os.sched_getaffinity(0))
-        self.wl = media.layered_salt(256, 15.0, 32, 2)
-        t0 = time.perf_counter()
+        self.wl = media.marmousi_1024()
         self.P = oop.Problem.from_workload(self.wl)
-        self.u0 = self.P.sources(self.wl.sources)
-        tree = oh.Tree(256, 256, 6, "quadtree")
-        A = oh.build(self.P, tree, 20, 10, 0, 1002)
-        self.H = oh.invert(A, 10, 1002)
-        self.t_build = time.perf_counter() - t0
+        self.u0 = self.P.sources(self.wl.sources[:1])
         self.k = 0
 
     def step(self):
-        s = self.k % self.u0.shape[1]
-        self.k += 1
         t0 = time.perf_counter()
-        x, it, res = self.osolve.fgmres(self.P, self.u0[:, s], lambda v: self.oh.apply(self.H, v), TOL, 30, 120)
+        y = self.oop.apply(self.oop.RESIDUAL, self.P.spec, self.P.chi, self.u0, self.u0, self.P.nz, self.P.nx)
         t = time.perf_counter() - t0
-        return t + self.t_build / self.u0.shape[1], res <= TOL
+        return t, bool(np.all(np.isfinite(y)))
 
-    def sample_text(self):
-        return ("same workload; HODLR build+inversion once (%.1f s, charged 1/32 per solve), then complete "
-                "one-source FGMRES(30) solves to 1e-6" % self.t_build)
+    def sample_text(self, applies_per_solve: float, n: int):
+        return ("same workload; %d FP64 RESIDUAL applies of I - G0 V on one 1024^2 source field (numpy FFT on "
+                "the 2048^2 padded grid) timed, scaled by %.1f applies per solve; the oracle's HODLR build and "
+                "apply (16 GB of complex128 leaves) are not run, so the value bounds the oracle from above"
+                % (n, applies_per_solve))
 
 
-def cpu_baseline():
-    """One oracle step (see OracleArm), reported with its sample."""
+def cpu_baseline(applies_per_solve: float = APPLIES_PER_SOLVE):
+    """A bounded oracle sample (see OracleArm), reported with its sample."""
     arm = OracleArm()
-    t, ok = arm.step()
-    return {"value": round((1.0 if ok else 0.0) / t, 5), "unit": "solves/s", "cores": arm.cores, "kind": "oracle",
-            "sample": arm.sample_text() + "; 1 solve timed"}
+    arm.step()
+    ts = [arm.step()[0] for _ in range(3)]
+    t_apply = float(np.mean(ts))
+    return {"value": round(1.0 / (applies_per_solve * t_apply), 6), "unit": "solves/s", "cores": arm.cores,
+            "kind": "oracle", "bound": "upper", "seconds_per_apply": round(t_apply, 4),
+            "sample": arm.sample_text(applies_per_solve, len(ts))}
 
 
 def run_reference(args):
@@ -480,34 +515,33 @@ def run_reference(args):
     arm = OracleArm()
     for _ in range(args.warmup):
         arm.step()
-    times, ok = [], 0
+    times = []
     for _ in range(args.steps):
         t, good = arm.step()
         times.append(t)
-        ok += int(good)
-    total = float(np.sum(times))
-    v = ok / total
-    line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "solves/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1),
+    t_apply = float(np.mean(times))
+    v = 1.0 / (APPLIES_PER_SOLVE * t_apply)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * APPLIES_PER_SOLVE * t_apply, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256x256", "h_m": 10.0, "freq_hz": 15.0,
-                       "preconditioner": "HODLR quadtree 32x32 leaves, 6 levels, rank 20+10, q=0, FP64",
-                       "solver": "FGMRES(30) right-preconditioned, FP64"},
-            "cpu_baseline": {"value": round(v, 5), "unit": "solves/s", "cores": arm.cores, "kind": "oracle",
-                             "sample": arm.sample_text() + f"; {args.steps} solves timed"},
-            "e2e": {"value": round(v, 5), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD, "grid": "1024x1024", "h_m": 5.0, "freq_hz": 30.0,
+                       "solver": "oracle FP64 operator applies only (bounded sample)"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "solves/s", "cores": arm.cores, "kind": "oracle",
+                             "bound": "upper", "sample": arm.sample_text(APPLIES_PER_SOLVE, args.steps)},
+            "e2e": {"value": round(v, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "anomaly-batched", "c128-one-at-a-time", "marmousi-1024",
-                                                              "marmousi-subset-sweep", "salt-subset-sweep"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "layered-salt-256", "anomaly-batched",
+                                                              "c128-one-at-a-time", "marmousi-subset-sweep",
+                                                              "salt-subset-sweep"],
                     help="the headline workload (default) or a further measured one")
     ap.add_argument("--rank-max", type=int, default=0, help="anomaly-batched: rank adaptation limit (0: off)")
     ap.add_argument("--sweep-method", default="series", choices=["series", "fgmres"],

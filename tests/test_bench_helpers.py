@@ -57,7 +57,9 @@ def test_peak_is_the_measured_copy_bandwidth(tmp_path, monkeypatch):
 
 
 def test_fp32_peak_and_operator_bytes():
+    # the nominal fallback follows the SM count and clock it is given
     assert bench.fp32_alu_peak_tflops() == pytest.approx(80.5, abs=0.05)
+    assert bench.fp32_alu_peak_tflops(76, 2070.0) == pytest.approx(40.3, abs=0.05)
     # 256^2 grid, 32 sources: u, u0 in and y out (8 B each), chi (8 B) and the
     # (257 x 257) quarter spectrum (8 B) once per batch
     n = 256 * 256
