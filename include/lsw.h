@@ -441,6 +441,23 @@ lsw_status lsw_fno_loss_grad(lsw_fno* f, const void* x, const void* target, int 
 /* One Adam update with the handle's gradients; t >= 1 is the step number
  * (bias corrections 1 - beta^t), so a resumed run passes its own count. */
 lsw_status lsw_fno_adam_step(lsw_fno* f, float lr, int32_t t, void* stream);
+/* Training pairs of the network (not part of the paper): for nbatch residual
+ * fields r and their corrections e = (I - G0 V)^-1 r (prec LSW_C128 or
+ * LSW_C64, device, nbatch x nz*nx), writes the inputs x (complex64, nbatch x 2
+ * fields: r / ||r||_2 and chi / k0^2 + i k0 h) and the targets t = e / ||r||_2
+ * (complex64, nbatch fields), ||r||_2 in FP64. */
+lsw_status lsw_fno_pairs(const lsw_green* g, const double* chi, const void* r, const void* e, int nbatch, int prec,
+                         void* x, void* t, void* stream);
+/* Phase augmentation of nbatch pairs in place: channel 0 of x_b and t_b are
+ * multiplied by exp(i phases[b]) (phases: HOST array of nbatch angles in
+ * radians, read before the call returns; the map r -> e is complex-linear,
+ * so a rotated pair is again a pair).  n = nz * nx.  Synchronises stream. */
+lsw_status lsw_fno_rotate(void* x, void* t, int nbatch, int64_t n, const float* phases, void* stream);
+/* The network's error on batch pairs: *num = sum |network(x) - t|^2 and
+ * *den = sum |t|^2 over every output (FP64 sums, HOST outputs; synchronises
+ * stream). */
+lsw_status lsw_fno_error(const lsw_fno* f, const void* x, const void* t, int batch, double* num, double* den,
+                         void* stream);
 /* The preconditioner: z_b = ||v_b|| * network([v_b / ||v_b||, chi/k0^2 + i k0 h])
  * for nbatch fields v (prec LSW_C128 or LSW_C64, device), on g's grid, which
  * must match the network's. */

@@ -227,6 +227,55 @@ __global__ void k_fno_output(const float2* __restrict__ y, const double* __restr
     }
 }
 
+// t_b = e_b / ||r_b|| (complex128 or complex64 in, complex64 out)
+template <typename C>
+__global__ void k_scale_rows(const C* __restrict__ e, const double* __restrict__ inv_norm, float2* __restrict__ t,
+                             long long n, int B) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * B; q += (long long)gridDim.x * blockDim.x) {
+        const double s = inv_norm[q / n];
+        t[q] = make_float2((float)(e[q].x * s), (float)(e[q].y * s));
+    }
+}
+
+// x_b channel 0 and t_b times exp(i phi_b)
+__global__ void k_rotate_pairs(float2* __restrict__ x, float2* __restrict__ t, const float2* __restrict__ rot,
+                               long long n, int B) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * B; q += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(q / n);
+        const long long i = q - (long long)b * n;
+        const float2 w = rot[b];
+        float2* xv = x + (long long)b * 2 * n + i;
+        const float2 a = *xv, c = t[q];
+        *xv = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+        t[q] = make_float2(c.x * w.x - c.y * w.y, c.x * w.y + c.y * w.x);
+    }
+}
+
+// per-block partial sums of |y - t|^2 and |t|^2 in FP64
+__global__ void __launch_bounds__(256) k_err_sums(const float2* __restrict__ y, const float2* __restrict__ t,
+                                                  long long tot, double* __restrict__ part) {
+    __shared__ double sn[8], sd[8];
+    double num = 0.0, den = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x) {
+        const float2 a = y[q], c = t[q];
+        const double dx = (double)a.x - c.x, dy = (double)a.y - c.y;
+        num += dx * dx + dy * dy;
+        den += (double)c.x * c.x + (double)c.y * c.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sn[threadIdx.x >> 5] = num; sd[threadIdx.x >> 5] = den; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) { a += sn[w]; b += sd[w]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
 __global__ void k_scale(float2* p, long long n, float a) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         p[e].x *= a;
@@ -577,6 +626,77 @@ lsw_status lsw_fno_adam_step(lsw_fno* f, float lr, int32_t t, void* stream) {
     k_adam<<<gridn(f->np), 256, 0, st>>>(f->params, f->grads, f->adam_m, f->adam_v, f->np, lr, (float)b1, (float)b2,
                                          1e-8f, c1_, c2_);
     LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+lsw_status lsw_fno_pairs(const lsw_green* g, const double* chi, const void* r, const void* e, int nbatch, int prec,
+                         void* x, void* t, void* stream) {
+    if (!g || !chi || !r || !e || !x || !t || nbatch <= 0 || (prec != LSW_C128 && prec != LSW_C64))
+        return LSW_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const long long n = (long long)g->nz * g->nx;
+    DevBuf n2, nrm, inv;
+    LSW_TRY(n2.alloc(sizeof(double) * nbatch, st));
+    LSW_TRY(nrm.alloc(sizeof(double) * nbatch, st));
+    LSW_TRY(inv.alloc(sizeof(double) * nbatch, st));
+    if (prec == LSW_C128) LSW_TRY(norms2<double>((const double2*)r, n, nbatch, n2.as<double>(), st));
+    else LSW_TRY(norms2<float>((const float2*)r, n, nbatch, n2.as<double>(), st));
+    k_sqrt_inv<<<(nbatch + 255) / 256, 256, 0, st>>>(n2.as<double>(), nrm.as<double>(), inv.as<double>(), nbatch);
+    LSW_LAUNCH_CHECK();
+    const double ik02 = 1.0 / (g->k * g->k);
+    const float k0h = (float)(g->k * g->h);
+    if (prec == LSW_C128) {
+        k_fno_input<double2><<<gridn(n * nbatch), 256, 0, st>>>((const double2*)r, inv.as<double>(), chi, ik02, k0h,
+                                                               (float2*)x, n, nbatch);
+        LSW_LAUNCH_CHECK();
+        k_scale_rows<double2><<<gridn(n * nbatch), 256, 0, st>>>((const double2*)e, inv.as<double>(), (float2*)t, n,
+                                                                nbatch);
+    } else {
+        k_fno_input<float2><<<gridn(n * nbatch), 256, 0, st>>>((const float2*)r, inv.as<double>(), chi, ik02, k0h,
+                                                              (float2*)x, n, nbatch);
+        LSW_LAUNCH_CHECK();
+        k_scale_rows<float2><<<gridn(n * nbatch), 256, 0, st>>>((const float2*)e, inv.as<double>(), (float2*)t, n,
+                                                               nbatch);
+    }
+    LSW_LAUNCH_CHECK();
+    return LSW_OK;
+}
+
+lsw_status lsw_fno_rotate(void* x, void* t, int nbatch, int64_t n, const float* phases, void* stream) {
+    if (!x || !t || !phases || nbatch <= 0 || n <= 0) return LSW_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<float2> w(nbatch);
+    for (int b = 0; b < nbatch; ++b) w[b] = make_float2((float)std::cos((double)phases[b]), (float)std::sin((double)phases[b]));
+    DevBuf rot;
+    LSW_TRY(rot.alloc(sizeof(float2) * nbatch, st));
+    LSW_CUDA(cudaMemcpyAsync(rot.p, w.data(), sizeof(float2) * nbatch, cudaMemcpyHostToDevice, st));
+    k_rotate_pairs<<<gridn((long long)n * nbatch), 256, 0, st>>>((float2*)x, (float2*)t, rot.as<float2>(), n, nbatch);
+    LSW_LAUNCH_CHECK();
+    // the host array w is read by the copy: wait before it goes out of scope
+    LSW_CUDA(cudaStreamSynchronize(st));
+    return LSW_OK;
+}
+
+lsw_status lsw_fno_error(const lsw_fno* f, const void* x, const void* t, int batch, double* num, double* den,
+                         void* stream) {
+    if (!f || !x || !t || !num || !den || batch <= 0) return LSW_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const long long tot = f->n * batch;
+    DevBuf y, part;
+    LSW_TRY(y.alloc(sizeof(float2) * tot, st));
+    const int nblk = 256;
+    LSW_TRY(part.alloc(sizeof(double) * 2 * nblk, st));
+    FnoTape tp;
+    LSW_TRY(fno_forward(f, (const float2*)x, y.as<float2>(), batch, tp, st));
+    k_err_sums<<<nblk, 256, 0, st>>>(y.as<float2>(), (const float2*)t, tot, part.as<double>());
+    LSW_LAUNCH_CHECK();
+    std::vector<double> h(2 * nblk);
+    LSW_CUDA(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * 2 * nblk, cudaMemcpyDeviceToHost, st));
+    LSW_CUDA(cudaStreamSynchronize(st));
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblk; ++i) { a += h[2 * i]; b += h[2 * i + 1]; }
+    *num = a;
+    *den = b;
     return LSW_OK;
 }
 

@@ -55,11 +55,6 @@ def _grid(n, freq):
     return lsw.build_green(n, n, H_CELL, media.C0, freq)
 
 
-def _second_channel(chi: torch.Tensor, freq: float) -> torch.Tensor:
-    k0 = 2 * math.pi * freq / media.C0
-    return (chi / k0 ** 2).to(torch.complex64) + 1j * (k0 * H_CELL)
-
-
 def residual_fields(G, chi, rng: np.random.Generator, count: int, n: int) -> torch.Tensor:
     """count residual-like fields (count, n * n) complex128 on the device."""
     k = count // 3
@@ -84,12 +79,9 @@ def make_pairs(n: int, seeds, per_medium: int, hp: lsw.HParams, tol: float = 1e-
                              max_outer=12)
         e, infos = lsw.solve_series(G, chi, H, r, sp=sp)
         ok = torch.tensor([i.status == 0 for i in infos], device="cuda")
-        nr = torch.linalg.vector_norm(r, dim=1, keepdim=True)
-        x = torch.empty((per_medium, 2, n * n), dtype=torch.complex64, device="cuda")
-        x[:, 0] = (r / nr).to(torch.complex64)
-        x[:, 1] = _second_channel(chi, f)
+        x, t = lsw.fno_pairs(G, chi, r, e)
         xs.append(x[ok])
-        ts.append((e / nr).to(torch.complex64)[ok])
+        ts.append(t[ok])
         if log:
             log(f"medium {seed}: f={f:.1f} Hz, {int(ok.sum())}/{per_medium} pairs, "
                 f"mean FGMRES iterations {np.mean([i.iterations for i in infos]):.1f}")
@@ -114,9 +106,7 @@ def train(net: lsw.FNO, pairs: Pairs, steps: int, batch: int, lr: float, seed: i
         idx = torch.from_numpy(rng.integers(0, N, size=b)).cuda()
         x, tgt = pairs.x[idx].contiguous(), pairs.t[idx].contiguous()
         if phase:
-            rot = torch.from_numpy(np.exp(1j * rng.uniform(0, 2 * np.pi, size=(b, 1))).astype(np.complex64)).cuda()
-            x[:, 0] *= rot
-            tgt *= rot
+            lsw.fno_rotate(x, tgt, rng.uniform(0, 2 * np.pi, size=b))
         loss = net.loss_grad(x, tgt)
         net.adam_step(lr_at(t, steps, lr), t)
         hist.append(loss)
@@ -129,10 +119,9 @@ def relative_error(net: lsw.FNO, pairs: Pairs, batch: int = 64) -> float:
     """sum ||y - t||^2 / sum ||t||^2 over a pair set."""
     num = den = 0.0
     for i in range(0, len(pairs), batch):
-        y = net.forward(pairs.x[i:i + batch].contiguous())
-        t = pairs.t[i:i + batch]
-        num += float(torch.linalg.vector_norm(y - t) ** 2)
-        den += float(torch.linalg.vector_norm(t) ** 2)
+        a, b = net.error_sums(pairs.x[i:i + batch].contiguous(), pairs.t[i:i + batch].contiguous())
+        num += a
+        den += b
     return math.sqrt(num / den)
 
 

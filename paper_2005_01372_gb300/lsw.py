@@ -129,6 +129,9 @@ _SIGS = {
     "lsw_fno_loss_grad": (I32, [VP, VP, VP, I32, ctypes.POINTER(ctypes.c_double), VP, VP]),
     "lsw_fno_adam_step": (I32, [VP, ctypes.c_float, ctypes.c_int32, VP]),
     "lsw_fno_apply": (I32, [VP, VP, VP, VP, VP, I32, I32, VP]),
+    "lsw_fno_pairs": (I32, [VP, VP, VP, VP, I32, I32, VP, VP, VP]),
+    "lsw_fno_rotate": (I32, [VP, VP, I32, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), VP]),
+    "lsw_fno_error": (I32, [VP, VP, VP, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), VP]),
     "lsw_solve_learned": (I32, [VP, VP, VP, VP, VP, VP, I32, ctypes.POINTER(_SolveParams),
                                 ctypes.POINTER(SolveInfo), VP]),
 }
@@ -550,6 +553,14 @@ class FNO:
                "lsw_fno_loss_grad")
         return (loss.value, g) if want_grad else loss.value
 
+    def error_sums(self, x: torch.Tensor, target: torch.Tensor, stream=None):
+        """lsw_fno_error: (sum |net(x) - target|^2, sum |target|^2)."""
+        num, den = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(lib().lsw_fno_error(self.handle, _ptr(x, torch.complex64), _ptr(target, torch.complex64),
+                                   int(target.shape[0]), ctypes.byref(num), ctypes.byref(den), _stream(stream)),
+               "lsw_fno_error")
+        return float(num.value), float(den.value)
+
     def adam_step(self, lr: float, t: int, stream=None):
         _check(lib().lsw_fno_adam_step(self._h, lr, t, _stream(stream)), "lsw_fno_adam_step")
 
@@ -561,6 +572,26 @@ class FNO:
         _check(lib().lsw_fno_apply(self._h, G.handle, _ptr(chi, torch.float64), _ptr(v, v.dtype), _ptr(z, v.dtype),
                                    nb, prec, _stream(stream)), "lsw_fno_apply")
         return z
+
+
+def fno_pairs(G: Green, chi, r, e, stream=None):
+    """lsw_fno_pairs: network inputs x (nb, 2, n) and targets t (nb, n),
+    complex64, from residuals r and corrections e (nb, n)."""
+    prec = C128 if r.dtype == torch.complex128 else C64
+    nb = r.numel() // G.n
+    x = torch.empty((nb, 2, G.n), dtype=torch.complex64, device=r.device)
+    t = torch.empty((nb, G.n), dtype=torch.complex64, device=r.device)
+    _check(lib().lsw_fno_pairs(G.handle, _ptr(chi, torch.float64), _ptr(r, r.dtype), _ptr(e, r.dtype), nb, prec,
+                               _ptr(x, torch.complex64), _ptr(t, torch.complex64), _stream(stream)), "lsw_fno_pairs")
+    return x, t
+
+
+def fno_rotate(x, t, phases, stream=None):
+    """lsw_fno_rotate: x[:, 0] and t times exp(i phases) in place."""
+    nb = t.shape[0]
+    ph = (ctypes.c_float * nb)(*[float(p) for p in phases])
+    _check(lib().lsw_fno_rotate(_ptr(x, torch.complex64), _ptr(t, torch.complex64), nb, int(t.shape[1]), ph,
+                                _stream(stream)), "lsw_fno_rotate")
 
 
 def solve_learned(G: Green, chi, fno: FNO, H, u0, u=None, sp: SolveParams = None, stream=None, check: bool = False):
