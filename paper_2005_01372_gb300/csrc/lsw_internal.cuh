@@ -210,18 +210,24 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
 
 // FP64 small-matrix arithmetic of the sketches (small64.cu).
 // Gram matrices of complex64 blocks with error-free products (Dot2), FP64 result.
-lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st);
+// Blocks b with active[b] == 0 are skipped (active may be NULL: all).
+lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st,
+                      const int* active = nullptr);
 // Rinv_b = R_b^-1 (upper triangular, k x k) with G_b + s I = R_b^H R_b, an
 // FP64 Cholesky factor, s = shift_rel tr(G_b) / k (raised on breakdown).
+// active (may be NULL) skips blocks; need2 (may be NULL) receives 1 where a
+// second Cholesky QR pass is needed (kappa_F > 1e3 or a shift was applied).
 template <typename R>
-lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st);
+lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st,
+                     const int* active = nullptr, int* need2 = nullptr);
 // Eigenvectors of the FP64 Hermitian G_b as the columns of V_b (k x k, FP32),
 // by decreasing eigenvalue, resolved to FP64 accuracy: FP32 Jacobi, an
 // FP64-accurate Rayleigh-Ritz projection B = V0^H G V0, FP32 Jacobi on the
 // nearly diagonal B, V = V0 Z.
 lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t st);
-// Thin QR of complex64 sketch blocks (Q in place): shifted Cholesky QR3 with
-// FP64 Grams and factors, or FP64 Householder for short blocks.
+// Thin QR of complex64 sketch blocks (Q in place): Cholesky QR with Dot2
+// Grams and products and FP64 factors, a second pass where the conditioning
+// asks for it; FP64 Householder for short blocks.
 lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaStream_t st);
 
 // Cast FP64 complex -> working precision.

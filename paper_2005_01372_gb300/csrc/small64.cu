@@ -61,10 +61,12 @@ constexpr int GT_MAXQ = 9;    // pairs per thread: 256 * 9 >= 64 * 65 / 2
 // for the upper-triangle pairs p.  Columns are staged in shared memory in
 // tiles of 32 rows (odd stride: the lanes of a warp read different banks).
 __global__ void __launch_bounds__(256)
-k_gram_c64(const float2* __restrict__ Y, int m, int k, long long sY, int nchunk, double2* __restrict__ part) {
+k_gram_c64(const float2* __restrict__ Y, int m, int k, long long sY, int nchunk, double2* __restrict__ part,
+           const int* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     float2* sy = reinterpret_cast<float2*>(sm_raw);   // k columns x (GT_ROWS + 1)
     const int b = blockIdx.y, ch = blockIdx.x;
+    if (active && !active[b]) return;                 // this block needs no second pass
     const int rows_per = (m + nchunk - 1) / nchunk;
     const int r0 = ch * rows_per, r1 = min(m, r0 + rows_per);
     const float2* Yb = Y + (long long)b * sY;
@@ -172,11 +174,13 @@ __device__ __forceinline__ double rsqrt64(double d) {
 
 template <typename C>
 __global__ void __launch_bounds__(128)
-k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel, C* __restrict__ Rall) {
+k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel, C* __restrict__ Rall,
+            const int* __restrict__ active, int* __restrict__ need2) {
     // one CTA (four warps, one per SM sub-partition and its FP64 unit) per matrix
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int tid = threadIdx.x, NT = blockDim.x;
     const int mat = blockIdx.x;
+    if (active && !active[mat]) return;
     const int ld = k + 1;
     double2* L = reinterpret_cast<double2*>(sm_raw);
     double2* X = L + (size_t)k * ld;
@@ -194,9 +198,12 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
     if (!(tr > 0.0) || !isfinite(tr)) {
         const double fill = (tr == 0.0) ? 0.0 : NAN;
         for (int e = tid; e < k * k; e += NT) { Rout[e].x = fill; Rout[e].y = fill; }
+        if (need2 && tid == 0) need2[mat] = 0;
         return;
     }
     double shift = shift_rel * tr;
+    const bool shifted0 = shift > 0.0;
+    int attempts = 0;
     bool ok = false;
     for (int attempt = 0; attempt < 13 && !ok; ++attempt) {
         for (int e = tid; e < k * k; e += NT) {
@@ -242,9 +249,11 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
         ok = fail == 0;
         __syncthreads();
         if (!ok) shift = shift > 0.0 ? shift * 100.0 : 1e-15 * tr;
+        ++attempts;
     }
     if (!ok) {
         for (int e = tid; e < k * k; e += NT) { Rout[e].x = NAN; Rout[e].y = NAN; }
+        if (need2 && tid == 0) need2[mat] = 0;
         return;
     }
     // X = L^-1 in axpy form, every column at once: X starts as I; step t
@@ -274,6 +283,7 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
         __syncthreads();
     }
     // Rinv(i, j) = conj(X(j, i)), upper triangular
+    double fro = 0.0;
     for (int e = tid; e < k * k; e += NT) {
         const int j = e / k, i = e - j * k;
         C v;
@@ -281,11 +291,78 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
             const double2 xv = X[i * ld + j];
             v.x = xv.x;
             v.y = -xv.y;
+            fro += xv.x * xv.x + xv.y * xv.y;
         } else {
             v.x = 0;
             v.y = 0;
         }
         Rout[e] = v;
+    }
+    if (need2) {
+        // kappa_F = ||Y||_F ||R^-1||_F >= kappa_2(Y).  One pass of Cholesky QR
+        // with an FP64-accurate Gram and product leaves Q^H Q - I ~ 1e-16
+        // kappa^2: a second pass is needed above kappa ~ 1e3 (and after any
+        // shift, which perturbs the factor on purpose).
+        for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = fro;
+        __syncthreads();
+        if (tid == 0) {
+            const double rf = red[0] + red[1] + red[2] + red[3];
+            const double kap2 = tr * k * rf;
+            need2[mat] = (shifted0 || attempts > 0 || !(kap2 <= 1e6)) ? 1 : 0;
+        }
+    }
+}
+
+// Q = Y R^-1 in place, formed with FP64 accuracy in FP32 arithmetic: R^-1
+// (FP64, upper triangular) is split into two FP32 parts, the products with
+// the high part are summed by Dot2 and those with the low part are added to
+// the compensation; the result is rounded to FP32 once.  Rows are
+// independent, so each CTA loads a tile of rows into shared memory and
+// writes its result over it.  Blocks whose active flag is 0 are skipped.
+__global__ void __launch_bounds__(256)
+k_rmul_dot2(float2* __restrict__ Y, int m, int k, long long sY, const double2* __restrict__ Rall,
+            const int* __restrict__ active) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int b = blockIdx.y;
+    if (active && !active[b]) return;
+    float2* Rh = reinterpret_cast<float2*>(sm_raw);   // k x k
+    float2* Rl = Rh + k * k;
+    float2* yt = Rl + k * k;                           // k columns x (GT_ROWS + 1)
+    const double2* R = Rall + (long long)b * k * k;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        const double2 v = R[e];
+        const float hx = (float)v.x, hy = (float)v.y;
+        Rh[e] = make_float2(hx, hy);
+        Rl[e] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    }
+    float2* Yb = Y + (long long)b * sY;
+    const int rows_per = (m + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * rows_per, r1 = min(m, r0 + rows_per);
+    for (int rr = r0; rr < r1; rr += GT_ROWS) {
+        const int nr = min(GT_ROWS, r1 - rr);
+        __syncthreads();
+        for (int e = threadIdx.x; e < GT_ROWS * k; e += blockDim.x) {
+            const int c = e / GT_ROWS, r = e - c * GT_ROWS;
+            yt[c * (GT_ROWS + 1) + r] = r < nr ? Yb[(long long)c * m + rr + r] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < GT_ROWS * k; e += blockDim.x) {
+            const int j = e / GT_ROWS, r = e - j * GT_ROWS;
+            if (r >= nr) continue;
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+            for (int t = 0; t <= j; ++t) {
+                const float2 a = yt[t * (GT_ROWS + 1) + r], h = Rh[j * k + t], l = Rl[j * k + t];
+                dot2(a.x, h.x, sr, cr);
+                dot2(-a.y, h.y, sr, cr);
+                dot2(a.x, h.y, si, ci);
+                dot2(a.y, h.x, si, ci);
+                cr = fmaf(a.x, l.x, fmaf(-a.y, l.y, cr));
+                ci = fmaf(a.x, l.y, fmaf(a.y, l.x, ci));
+            }
+            Yb[(long long)j * m + rr + r] = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+        }
     }
 }
 
@@ -381,7 +458,8 @@ __global__ void k_down32(const double2* __restrict__ s, float2* __restrict__ d, 
 
 }  // namespace
 
-lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st) {
+lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, double2* G, cudaStream_t st,
+                      const int* active) {
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
     const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
@@ -390,7 +468,7 @@ lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, do
     LSW_TRY(part.alloc(sizeof(double2) * (size_t)batch * nchunk * npair, st));
     KTimer kt("gram", st, 8.0 * batch * (double)m * k, 0.0);
     k_gram_c64<<<dim3(nchunk, batch), 256, sizeof(float2) * (GT_ROWS + 1) * k, st>>>(Y, m, k, sY, nchunk,
-                                                                                        part.as<double2>());
+                                                                                        part.as<double2>(), active);
     LSW_LAUNCH_CHECK();
     k_gram_c64_reduce<<<grid_small((long long)batch * k * k), 256, 0, st>>>(part.as<double2>(), nchunk, k, batch, G);
     LSW_LAUNCH_CHECK();
@@ -398,7 +476,8 @@ lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, do
 }
 
 template <typename R>
-lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st) {
+lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st,
+                     const int* active, int* need2) {
     typedef typename Cx<R>::T C;
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
@@ -409,7 +488,7 @@ lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typen
         attr.store(true);
     }
     KTimer kt("chol", st, 0.0, 0.0);
-    k_chol_rinv<C><<<batch, 128, per, st>>>(G, k, batch, shift_rel, Rinv);
+    k_chol_rinv<C><<<batch, 128, per, st>>>(G, k, batch, shift_rel, Rinv, active, need2);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
@@ -438,11 +517,15 @@ lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t 
 }
 
 // Thin QR of complex64 sketch blocks, Q returned in place of A (m x k, ld m,
-// block stride sA).  Tall blocks (m >= 4k): shifted Cholesky QR3 (Fukaya,
-// Nakatsukasa, Yanagisawa, Yamamoto, SIAM J. Sci. Comput. 42, 2020): one pass
-// on G + s I with s = 1e-13 tr(G) / k, then two plain passes, each an FP64
-// Gram, an FP64 Cholesky factor and a product with R^-1 in the data's
-// precision.  Short blocks: Householder QR in FP64 on an upcast copy.
+// block stride sA).  Tall blocks (m >= 4k): Cholesky QR with FP64-accurate
+// arithmetic in every step (Yamamoto, Nakatsukasa, Yanagisawa, Fukaya 2015,
+// with the Gram and the product both accurate to ~1e-16): G = Y^H Y by
+// Dot2, G + s I = R^H R in FP64 (s = 0, raised only on breakdown), Q = Y R^-1
+// by Dot2 products in place.  Then Q^H Q - I ~ 1e-16 kappa(Y)^2 + u32, so a
+// second identical pass on Q runs only for the blocks whose estimate
+// kappa_F = ||Y||_F ||R^-1||_F exceeds 1e3 or whose factor needed a shift
+// (a per-block flag on the device; the other blocks skip it).  Short blocks:
+// Householder QR in FP64 on an upcast copy.
 lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaStream_t st) {
     if (batch <= 0 || k <= 0 || m <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
@@ -457,27 +540,31 @@ lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaS
         LSW_LAUNCH_CHECK();
         return LSW_OK;
     }
-    KTimer kt("qr", st, 8.0 * batch * (double)mk * 7, 3.0 * batch * (8.0 * m * k * (k + 1) / 2 * 5 + 8.0 * m * k * k / 2));
-    DevBuf G, Ri, W;
+    KTimer kt("qr", st, 8.0 * batch * (double)mk * 4, 2.0 * batch * (8.0 * m * k * (k + 1) / 2 * 5 * 2));
+    DevBuf G, Ri, flag;
     LSW_TRY(G.alloc(sizeof(double2) * (size_t)batch * k * k, st));
-    LSW_TRY(Ri.alloc(sizeof(float2) * (size_t)batch * k * k, st));
-    LSW_TRY(W.alloc(sizeof(float2) * (size_t)mk * batch, st));
-    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-    auto pass = [&](const float2* src, long long ss, float2* dst, long long sd, double shift) -> lsw_status {
-        LSW_TRY(gram64_c64(src, m, k, ss, batch, G.as<double2>(), st));
-        LSW_TRY(chol_rinv<float>(G.as<double2>(), k, batch, shift, Ri.as<float2>(), st));
-        return gemm<float>('N', 'N', m, k, k, one, src, m, ss, Ri.as<float2>(), k, (long long)k * k, zero, dst, m, sd,
-                           batch, st);
+    LSW_TRY(Ri.alloc(sizeof(double2) * (size_t)batch * k * k, st));
+    LSW_TRY(flag.alloc(sizeof(int) * (size_t)batch, st));
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        LSW_CUDA(cudaFuncSetAttribute(k_rmul_dot2, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        attr.store(true);
+    }
+    const size_t smp = sizeof(float2) * (2 * (size_t)k * k + (size_t)(GT_ROWS + 1) * k);
+    const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
+    auto pass = [&](const int* active, int* need2) -> lsw_status {
+        LSW_TRY(gram64_c64(A, m, k, sA, batch, G.as<double2>(), st, active));
+        LSW_TRY(chol_rinv<double>(G.as<double2>(), k, batch, 0.0, Ri.as<double2>(), st, active, need2));
+        k_rmul_dot2<<<dim3(nchunk, batch), 256, smp, st>>>(A, m, k, sA, Ri.as<double2>(), active);
+        LSW_LAUNCH_CHECK();
+        return LSW_OK;
     };
-    LSW_TRY(pass(A, sA, W.as<float2>(), mk, 1e-13));
-    LSW_TRY(pass(W.as<float2>(), mk, A, sA, 0.0));
-    LSW_TRY(pass(A, sA, W.as<float2>(), mk, 0.0));
-    LSW_CUDA(cudaMemcpy2DAsync(A, sizeof(float2) * (size_t)sA, W.p, sizeof(float2) * (size_t)mk,
-                               sizeof(float2) * (size_t)mk, batch, cudaMemcpyDeviceToDevice, st));
+    LSW_TRY(pass(nullptr, flag.as<int>()));
+    LSW_TRY(pass(flag.as<int>(), nullptr));
     return LSW_OK;
 }
 
-template lsw_status chol_rinv<float>(const double2*, int, int, double, float2*, cudaStream_t);
-template lsw_status chol_rinv<double>(const double2*, int, int, double, double2*, cudaStream_t);
+template lsw_status chol_rinv<float>(const double2*, int, int, double, float2*, cudaStream_t, const int*, int*);
+template lsw_status chol_rinv<double>(const double2*, int, int, double, double2*, cudaStream_t, const int*, int*);
 
 }  // namespace lsw
