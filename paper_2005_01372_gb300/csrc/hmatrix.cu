@@ -527,17 +527,31 @@ k_lr_partial(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ X, i
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = czero<C>();
+    // the next tile's loads are issued into registers before the current
+    // tile's products (rs, ks <= 64: at most 8 entries of each per thread)
+    C fpre[8], xpre[8];
+    auto fetch = [&](int r0) {
+        const int nr = min(TR, CH - r0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = threadIdx.x + u * 256;
+            const int cc = e / TR, rr = e - cc * TR;
+            fpre[u] = (e < TR * rs && rr < nr && cc < r) ? ldfac(Fj + (long long)cc * nb + r0 + rr) : czero<C>();
+            xpre[u] = (e < TR * ks && rr < nr && cc < k) ? Xg[(long long)cc * m + r0 + rr] : czero<C>();
+        }
+    };
+    fetch(0);
     for (int r0 = 0; r0 < CH; r0 += TR) {
         const int nr = min(TR, CH - r0);
-        for (int e = threadIdx.x; e < TR * rs; e += 256) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = threadIdx.x + u * 256;
             const int cc = e / TR, rr = e - cc * TR;
-            Fs[rr * fsd + cc] = (rr < nr && cc < r) ? ldfac(Fj + (long long)cc * nb + r0 + rr) : czero<C>();
-        }
-        for (int e = threadIdx.x; e < TR * ks; e += 256) {
-            const int cc = e / TR, rr = e - cc * TR;
-            Xs[rr * xsd + cc] = (rr < nr && cc < k) ? Xg[(long long)cc * m + r0 + rr] : czero<C>();
+            if (e < TR * rs) Fs[rr * fsd + cc] = fpre[u];
+            if (e < TR * ks) Xs[rr * xsd + cc] = xpre[u];
         }
         __syncthreads();
+        if (r0 + TR < CH) fetch(r0 + TR);
         if (active) {
             for (int rr = rg; rr < nr; rr += G) {
                 C f[4], x[4];
@@ -603,6 +617,8 @@ k_lr_apply(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ T, int
     if (i0 >= m) return;
     const int c0 = g * 8;
     const long long nout = (long long)r * k;
+    // four factor columns' loads in flight (one for FP64, where registers run out)
+    constexpr int UNR = sizeof(C) == 16 ? 1 : 4;
     C acc[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -614,6 +630,7 @@ k_lr_apply(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ T, int
         const int bb = swapC ? (b ^ 1) : b;
         const FT* Gb = lv.G[q] + (long long)bb * nb * r + o;
         const C* Tb = T + (lv.t0[q] + bb) * nout;
+#pragma unroll UNR
         for (int t = 0; t < r; ++t) {
             C gv[4], tv[8];
 #pragma unroll
@@ -653,6 +670,9 @@ lsw_status lr_launch(const LrLevels<C, FT>& lv, int m, int r, int k, const C* X,
     const int rs = (r + 3) & ~3, ks = (k + 3) & ~3;
     const int Gr = std::max(1, 256 / ((rs / 4) * (ks / 4)));
     const size_t smem = sizeof(C) * (32 * (size_t)(rs + ks + 2) + (size_t)Gr * r * k);
+    // both factors of every level once, X once per level, Y read and written
+    KTimer kt("lr_levels", st, (double)lv.nlev * m * (2.0 * r * sizeof(FT) + (double)k * sizeof(C)) + 2.0 * m * k * sizeof(C),
+              8.0 * 2.0 * lv.nlev * (double)m * r * k);
     k_lr_partial<C, FT><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
     LSW_LAUNCH_CHECK();
     k_lr_reduce<C, FT><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
@@ -691,7 +711,7 @@ lsw_status lr_levels(const HStore<R>& H, int l, int c, bool F_is_W, const typena
         lv.F[q] = F_is_W ? W0 : U0;
         lv.G[q] = F_is_W ? U0 : W0;
         lv.nb[q] = nb;
-        lv.ch[q] = std::min(nb, 256);
+        lv.ch[q] = std::min(nb, 1024);
         lv.chunk0[q + 1] = lv.chunk0[q] + m / lv.ch[q];
         lv.t0[q + 1] = lv.t0[q] + cnt;
     }
@@ -1185,7 +1205,7 @@ lsw_status hmv_bf16(const HStoreB& B, const float2* X, int k, float2* Y, cudaStr
             lv.F[q] = B.W[lp];
             lv.G[q] = B.U[lp];
             lv.nb[q] = nb;
-            lv.ch[q] = std::min(nb, 256);
+            lv.ch[q] = std::min(nb, 1024);
             lv.chunk0[q + 1] = lv.chunk0[q] + n / lv.ch[q];
             lv.t0[q + 1] = lv.t0[q] + cnt;
         }

@@ -929,13 +929,14 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     // run (a nearly diagonal input whose small eigenvalues must be resolved
     // relative to themselves) stops only on a sweep without rotations and
     // uses a tighter pair threshold.
-    const R tol = polish ? (R)0 : (sizeof(R) == 8 ? (R)1e-26 : (R)1e-11);
-    const R skip = polish ? (sizeof(R) == 8 ? (R)1e-15 : (R)2e-7) : jacobi_skip<R>();
+    // polish 2 (coarse): a first pass that a polish run will finish
+    const R tol = polish == 1 ? (R)0 : polish == 2 ? (R)1e-6 : (sizeof(R) == 8 ? (R)1e-26 : (R)1e-11);
+    const R skip = polish == 1 ? (sizeof(R) == 8 ? (R)1e-15 : (R)2e-7) : jacobi_skip<R>();
     // the trace-scaled input is known to ~1e-16 absolute (an FP64-accurate
     // matrix): entries below that are noise and never trigger a rotation, so
     // a polish of a matrix with (near-)zero eigenvalues still ends
-    const R floor_abs = polish ? (R)1e-15 : (R)0;
-    for (int sweep = 0; sweep < (polish ? 20 : 40); ++sweep) {
+    const R floor_abs = polish == 1 ? (R)1e-15 : (R)0;
+    for (int sweep = 0; sweep < (polish == 1 ? 20 : 40); ++sweep) {
         C part = czero<C>();
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
             const C a = A[e];
@@ -1075,13 +1076,14 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
     }
     __syncwarp();
     // the same stopping rules as the CTA version
-    const R tol = polish ? (R)0 : (sizeof(R) == 8 ? (R)1e-26 : (R)1e-11);
-    const R skip = polish ? (sizeof(R) == 8 ? (R)1e-15 : (R)2e-7) : jacobi_skip<R>();
+    // polish 2 (coarse): a first pass that a polish run will finish
+    const R tol = polish == 1 ? (R)0 : polish == 2 ? (R)1e-6 : (sizeof(R) == 8 ? (R)1e-26 : (R)1e-11);
+    const R skip = polish == 1 ? (sizeof(R) == 8 ? (R)1e-15 : (R)2e-7) : jacobi_skip<R>();
     // the trace-scaled input is known to ~1e-16 absolute (an FP64-accurate
     // matrix): entries below that are noise and never trigger a rotation, so
     // a polish of a matrix with (near-)zero eigenvalues still ends
-    const R floor_abs = polish ? (R)1e-15 : (R)0;
-    for (int sweep = 0; sweep < (polish ? 20 : 40); ++sweep) {
+    const R floor_abs = polish == 1 ? (R)1e-15 : (R)0;
+    for (int sweep = 0; sweep < (polish == 1 ? 20 : 40); ++sweep) {
         R off = 0, tot = 0;
         for (int e = lane; e < k * k; e += 32) {
             const C a = A[e];

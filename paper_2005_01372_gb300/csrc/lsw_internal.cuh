@@ -202,9 +202,11 @@ lsw_status gram64(const typename Cx<R>::T* Y, int m, int k, long long sY, int ba
 
 // Batched Hermitian eigenvectors by cyclic Jacobi in precision R: V_b (k x k)
 // receives the eigenvectors of the FP64 matrix G_b as columns, sorted by
-// decreasing eigenvalue.  polish != 0: for a nearly diagonal G whose small
+// decreasing eigenvalue.  polish 1: for a nearly diagonal G whose small
 // eigenvalues are to be resolved relative to themselves (no global stop on
-// the off-diagonal norm, a tighter pair threshold).
+// the off-diagonal norm, a tighter pair threshold); polish 2: a coarse first
+// pass (stop at a relative squared off-diagonal norm of 1e-6) for a polish
+// run to finish.
 template <typename R>
 lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch, cudaStream_t st, int polish = 0);
 
@@ -221,9 +223,9 @@ template <typename R>
 lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typename Cx<R>::T* Rinv, cudaStream_t st,
                      const int* active = nullptr, int* need2 = nullptr);
 // Eigenvectors of the FP64 Hermitian G_b as the columns of V_b (k x k, FP32),
-// by decreasing eigenvalue, resolved to FP64 accuracy: FP32 Jacobi, an
-// FP64-accurate Rayleigh-Ritz projection B = V0^H G V0, FP32 Jacobi on the
-// nearly diagonal B, V = V0 Z.
+// by decreasing eigenvalue, resolved to FP64 accuracy: a coarse FP32 Jacobi
+// (V0), an FP64-accurate Rayleigh-Ritz projection B = V0^H G V0, FP32 Jacobi
+// on the nearly diagonal B, V = V0 Z.
 lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t st);
 // Thin QR of complex64 sketch blocks (Q in place): Cholesky QR with Dot2
 // Grams and products and FP64 factors, a second pass where the conditioning

@@ -502,7 +502,7 @@ lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t 
     LSW_TRY(V0.alloc(sizeof(float2) * kk * batch, st));
     LSW_TRY(B.alloc(sizeof(double2) * kk * batch, st));
     LSW_TRY(Z.alloc(sizeof(float2) * kk * batch, st));
-    LSW_TRY(heev_jacobi<float>(G, V0.as<float2>(), k, batch, st, 0));
+    LSW_TRY(heev_jacobi<float>(G, V0.as<float2>(), k, batch, st, 2));
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         LSW_CUDA(cudaFuncSetAttribute(k_rr_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
