@@ -332,6 +332,9 @@ def run_extra(args):
       +10 after a failure within 30 iterations or a solve that needed more
       than 10, at most 50), and the paper's preconditioned series in FP32
       inside FP64 refinement to 1e-6 (--sweep-method fgmres: FGMRES(30)).
+    c128-one-at-a-time-1024: the headline 1024^2 workload on the plain FP64
+      path: c128 operator, HODLR in FP64 at the same rank, FGMRES(30) in FP64,
+      one source per solve call, the build in every step.
     c128-one-at-a-time: the 256^2 salt workload on the plain FP64
       path, one source per solve call: c128 operator, HODLR in FP64, FGMRES(30)
       in FP64; the build is charged once per 32 sources."""
@@ -411,6 +414,25 @@ def run_extra(args):
                "preconditioner": f"HODLR 32x32 leaves, {levels} levels, FP32, rank 10..50 by the paper's policy",
                "solver": ("FGMRES(30)" if m == lsw.FGMRES else "preconditioned series (<= 30 steps)")
                + " in FP64 refinement to 1e-6, lsw_solve_sweep"}
+    elif args.workload == "c128-one-at-a-time-1024":
+        wl = media.marmousi_1024()
+        vel = torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).to(dev)
+        hp = lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C128, levels=LEVELS, rank=RANK, oversample=OVERSAMPLE,
+                         seed=SEED)
+        sp = lsw.SolveParams(prec=lsw.C128, method=lsw.FGMRES, tol=TOL, restart=30, max_iter=1200)
+
+        def step():
+            G = lsw.build_green(wl.nz, wl.nx, wl.h, wl.c0, wl.freq_hz)
+            chi = G.contrast(vel)
+            H = lsw.build_hmatrix(G, chi, hp)
+            ok = 0
+            for s in wl.sources:
+                u0 = G.point_sources([s], lsw.C128)
+                _, inf = lsw.solve_series(G, chi, H, u0, sp=sp)
+                ok += sum(1 for i in inf if i.status == 0 and i.rel_residual <= TOL)
+            return ok, len(wl.sources), None
+        cfg = {"workload": WORKLOAD, "path": "c128 operator, FP64 HODLR (rank 40+10), FP64 FGMRES(30), one source "
+                                             "per call"}
     else:
         wl = media.layered_salt(256, 15.0, 32, 2)
         vel = torch.from_numpy(np.ascontiguousarray(wl.velocity.ravel())).to(dev)
@@ -540,8 +562,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "layered-salt-256", "anomaly-batched",
-                                                              "c128-one-at-a-time", "marmousi-subset-sweep",
-                                                              "salt-subset-sweep"],
+                                                              "c128-one-at-a-time", "c128-one-at-a-time-1024",
+                                                              "marmousi-subset-sweep", "salt-subset-sweep"],
                     help="the headline workload (default) or a further measured one")
     ap.add_argument("--rank-max", type=int, default=0, help="anomaly-batched: rank adaptation limit (0: off)")
     ap.add_argument("--sweep-method", default="series", choices=["series", "fgmres"],

@@ -20,6 +20,7 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "lsw_internal.cuh"
@@ -474,24 +475,12 @@ lsw_status build_level(const lsw_green* g, const double* chi, const Tree& tr, in
 // (X, Y: m x k, ld m, m = the node's rows).  Three launches: partial T over
 // row chunks of every level, the fixed-order reduction of the partials, and
 // one pass over Y adding every level's G T.
-constexpr int kMaxLev = 16;
-
 // factor entries as stored (complex FP32 / FP64, or a BF16 pair in 32 bits)
 __device__ __forceinline__ float2 ldfac(const float2* p) { return *p; }
 __device__ __forceinline__ double2 ldfac(const double2* p) { return *p; }
 __device__ __forceinline__ float2 ldfac(const uint32_t* p) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
 }
-
-template <typename C, typename FT = C> struct LrLevels {
-    const FT* F[kMaxLev];
-    const FT* G[kMaxLev];
-    int nb[kMaxLev];
-    int ch[kMaxLev];                // rows per chunk (divides nb)
-    int chunk0[kMaxLev + 1];        // first chunk of each level
-    long long t0[kMaxLev + 1];      // first T block of each level (units of r*k)
-    int nlev;
-};
 
 // Partial T over one chunk of CH rows: out (r x k) = F_chunk^H X_chunk.
 // Rows go through shared memory in tiles of 32, stored row-major so that a
@@ -673,10 +662,22 @@ lsw_status lr_launch(const LrLevels<C, FT>& lv, int m, int r, int k, const C* X,
     // both factors of every level once, X once per level, Y read and written
     KTimer kt("lr_levels", st, (double)lv.nlev * m * (2.0 * r * sizeof(FT) + (double)k * sizeof(C)) + 2.0 * m * k * sizeof(C),
               8.0 * 2.0 * lv.nlev * (double)m * r * k);
-    k_lr_partial<C, FT><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
-    LSW_LAUNCH_CHECK();
+    // BF16 factors and complex64 vectors: on the tensor cores when the shapes allow
+    bool tc = false;
+    if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value) tc = lr_tc_fits(lv, m, r, k);
+    if (tc) {
+        if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value)
+            LSW_TRY(lr_partial_tc(lv, m, r, k, X, swapA, P.as<C>(), st));
+    } else {
+        k_lr_partial<C, FT><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
+        LSW_LAUNCH_CHECK();
+    }
     k_lr_reduce<C, FT><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
     LSW_LAUNCH_CHECK();
+    if (tc) {
+        if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value)
+            return lr_apply_tc(lv, m, r, k, T.as<C>(), swapC, Y, st);
+    }
     const int rows_cta = 4 * (128 / ((k + 7) / 8));
     k_lr_apply<C, FT><<<(m + rows_cta - 1) / rows_cta, 128, 0, st>>>(lv, m, r, k, T.as<C>(), swapC, Y);
     LSW_LAUNCH_CHECK();

@@ -260,6 +260,28 @@ bool tc_bf16_fits(int M, int N, int K);
 lsw_status cgemm_tc_bf16(const uint32_t* A, int lda, long long sA, const float2* B, int ldb, long long sB, float2* C,
                          int ldc, long long sC, int M, int N, int K, float2 alpha, int batch, cudaStream_t st);
 
+// ------------------------------------------- H-matrix level products
+// Every level of a subtree product at once: level q has blocks of nb[q] rows
+// whose factors F_j, G_j (nb x r, column-major) are consecutive; rows are cut
+// into chunks of ch[q] for the partial products (hmatrix.cu, lr_tc.cu).
+constexpr int kMaxLev = 16;
+template <typename C, typename FT = C> struct LrLevels {
+    const FT* F[kMaxLev];
+    const FT* G[kMaxLev];
+    int nb[kMaxLev];
+    int ch[kMaxLev];                // rows per chunk (divides nb)
+    int chunk0[kMaxLev + 1];        // first chunk of each level
+    long long t0[kMaxLev + 1];      // first T block of each level (units of r*k)
+    int nlev;
+};
+// tcgen05 forms for BF16 factors (lr_tc.cu): the partials P = F^H X per
+// chunk, and Y += sum over levels of G T.
+bool lr_tc_fits(const LrLevels<float2, uint32_t>& lv, int m, int r, int k);
+lsw_status lr_partial_tc(const LrLevels<float2, uint32_t>& lv, int m, int r, int k, const float2* X, int swapA,
+                         float2* P, cudaStream_t st);
+lsw_status lr_apply_tc(const LrLevels<float2, uint32_t>& lv, int m, int r, int k, const float2* T, int swapC,
+                       float2* Y, cudaStream_t st);
+
 // Per-field FP64 squared 2-norms: out[b] = sum |x_b|^2 over n entries.
 template <typename R>
 lsw_status norms2(const typename Cx<R>::T* x, long long n, int batch, double* out, cudaStream_t st);

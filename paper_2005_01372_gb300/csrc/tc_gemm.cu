@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "lsw_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace lsw {
 namespace {
@@ -43,67 +44,9 @@ constexpr uint32_t TC_TMEM_COLS = 64;
 // N / 8 at bits 17-22, M / 16 at bits 24-28.
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_NN >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
-constexpr int TC_WAIT_LIMIT = 1 << 22;          // mbarrier polls before giving up
-
 __device__ int g_tc_timeouts = 0;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    hi = __uint_as_float(h);
-    lo = x - hi;
-}
-
-// byte offset of core-matrix row (row, kgroup) in a K-major tile of 8 kgroups
-__device__ __forceinline__ int kmaj(int row, int kg) { return (((row >> 3) << 3) + kg) * 128 + (row & 7) * 16; }
-
-// shared-memory matrix descriptor: start >> 4, LBO = 128 B (next core matrix
-// along K), SBO = 1024 B (next 8 rows), descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           (1ull << 46);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        :
-        : "r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+using namespace tcx;
 
 __global__ void __launch_bounds__(128)
 k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __restrict__ B, int ldb, long long sB,
@@ -193,9 +136,9 @@ k_cgemm_tc(const float2* __restrict__ A, int lda, long long sA, const float2* __
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t o = ks * 256;    // 8 real K = two core matrices
-                mma_tf32(tmem, sdesc(ah + o), sdesc(bh + o), (s > 0 || ks > 0) ? 1u : 0u);
-                mma_tf32(tmem, sdesc(ah + o), sdesc(bl + o), 1u);
-                mma_tf32(tmem, sdesc(al + o), sdesc(bh + o), 1u);
+                mma_tf32(tmem, sdesc(ah + o), sdesc(bh + o), TC_IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+                mma_tf32(tmem, sdesc(ah + o), sdesc(bl + o), TC_IDESC, 1u);
+                mma_tf32(tmem, sdesc(al + o), sdesc(bh + o), TC_IDESC, 1u);
             }
             mma_commit(buf ? mb1 : mb0);
         }
@@ -255,25 +198,6 @@ constexpr int TB_SMEM = 2 * TB_STAGE + 64;
 // D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), K-major, N / 8, M / 16
 constexpr uint32_t TB_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NN >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        :
-        : "r"(tmem), "l"(da), "l"(db), "r"(TB_IDESC), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void split_bf16(float x, float& hi, float& lo) {
-    hi = __bfloat162float(__float2bfloat16_rn(x));
-    lo = x - hi;
-}
 
 __global__ void __launch_bounds__(128)
 k_cgemm_tc_bf16(const uint32_t* __restrict__ A, int lda, long long sA, const float2* __restrict__ B, int ldb,
@@ -359,8 +283,8 @@ k_cgemm_tc_bf16(const uint32_t* __restrict__ A, int lda, long long sA, const flo
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t o = ks * 256;    // 16 BF16 of K = two core matrices
-                mma_bf16(tmem, sdesc(a + o), sdesc(bh + o), (s > 0 || ks > 0) ? 1u : 0u);
-                mma_bf16(tmem, sdesc(a + o), sdesc(bl + o), 1u);
+                mma_bf16(tmem, sdesc(a + o), sdesc(bh + o), TB_IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+                mma_bf16(tmem, sdesc(a + o), sdesc(bl + o), TB_IDESC, 1u);
             }
             mma_commit(buf ? mb1 : mb0);
         }

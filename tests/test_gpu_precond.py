@@ -334,7 +334,7 @@ def test_hodlr_power_iteration_parity_c128(lsw):
     assert _rel(y, ref.apply(x.T).T) < 1e-10
 
 
-@pytest.mark.parametrize("n,L,k", [(64, 2, 32), (64, 2, 40), (32, 4, 5)])
+@pytest.mark.parametrize("n,L,k", [(64, 2, 32), (64, 2, 40), (32, 4, 5), (128, 4, 16)])
 def test_bf16_storage_matches_fp32_storage(lsw, n, L, k):
     """H built in FP32 and kept as BF16 (re, im) pairs: every stored entry is
     rounded to 8 significant bits (relative error <= 2^-9 ~ 2e-3), and the
