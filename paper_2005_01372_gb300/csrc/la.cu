@@ -435,7 +435,7 @@ __device__ __forceinline__ C block_sum(C v, C* red) {
     __syncthreads();
     C s = czero<C>();
     if (threadIdx.x < 32) {
-        s = threadIdx.x < NT / 32 ? red[threadIdx.x] : czero<C>();
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : czero<C>();
         for (int o = 16; o > 0; o >>= 1) {
             s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
             s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
@@ -891,9 +891,15 @@ template <typename R> __device__ __forceinline__ R jacobi_skip() { return sizeof
 // index pairs chosen by the circle method, so every pair is met once per
 // sweep.  Input: FP64 Hermitian G (k x k), scaled by its trace; output: the
 // eigenvectors as columns of V, by decreasing eigenvalue.
-#define JACOBI_COUNT_ROTATION atomicAdd(&nrot, 1)
+// sort key of an eigenvalue: a NaN sorts last, so that the ranks of any k
+// values (ties broken by index) are a permutation of 0 .. k-1
 template <typename R>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ R jacobi_key(R d) { return isnan(d) ? -INFINITY : d; }
+
+#define JACOBI_COUNT_ROTATION atomicAdd(&nrot, 1)
+#define JACOBI_MARK_ROUND (rf[r & 1] = 1)
+template <typename R>
+__global__ void __launch_bounds__(1024)
 k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int polish) {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -913,10 +919,11 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     const double2* G = Gall + (long long)blockIdx.x * k * k;
     // e / k for e < k * k <= 4096 by a multiply and a shift (exact for k < 256)
     const unsigned kinv = (1u << 20) / (unsigned)k + 1u;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double t = 0;
-        for (int i = 0; i < k; ++i) t += fabs(G[i * k + i].x);
-        trs = t > 0 ? 1.0 / t : 0.0;
+        for (int i = threadIdx.x; i < k; i += 32) t += fabs(G[i * k + i].x);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) trs = t > 0 ? 1.0 / t : 0.0;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
@@ -936,16 +943,31 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     // matrix): entries below that are noise and never trigger a rotation, so
     // a polish of a matrix with (near-)zero eigenvalues still ends
     const R floor_abs = polish == 1 ? (R)1e-15 : (R)0;
+    __shared__ int rf[2];               // per round (alternating): some pair rotates
     for (int sweep = 0; sweep < (polish == 1 ? 20 : 40); ++sweep) {
+        // both flags clear before the sweep's first round (the block sum
+        // below synchronises; the previous round's reads ended at its last barrier)
+        if (threadIdx.x < 2) rf[threadIdx.x] = 0;
         C part = czero<C>();
+        int need = 0;                   // some pair is above the rotation threshold
         for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
             const C a = A[e];
             const R v = a.x * a.x + a.y * a.y;
             part.y += v;
-            if ((e % k) != (e / k)) part.x += v;
+            const int b = (int)(((unsigned)e * kinv) >> 20), aa = e - b * k;
+            if (aa != b) {
+                part.x += v;
+                if (aa < b) {
+                    const R app = A[aa * k + aa].x, aqq = A[b * k + b].x, ac = sqrt(v);
+                    if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
+                        ac > floor_abs && ac > 0)
+                        need = 1;
+                }
+            }
         }
-        const C on = block_sum<C, 256>(part, red);
+        const C on = block_sum<C, 1024>(part, red);
         if (!(on.x > tol * on.y) || on.y == 0) break;
+        if (!__syncthreads_or(need)) break;     // no pair would rotate: converged
         if (threadIdx.x == 0) nrot = 0;
         for (int r = 0; r < m - 1; ++r) {
             for (int i = threadIdx.x; i < m / 2; i += blockDim.x) {
@@ -969,6 +991,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                     if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
                         ac > floor_abs && ac > 0) {
                         JACOBI_COUNT_ROTATION;
+                        JACOBI_MARK_ROUND;
                         const R tau = (aqq - app) / (2 * ac);
                         const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
                         cs = (R)1 / sqrt((R)1 + t * t);
@@ -996,11 +1019,14 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 }
             }
             __syncthreads();
+            // a round without a rotation leaves A and V as they are
+            const bool any = rf[r & 1] != 0;
+            if (threadIdx.x == 0) rf[(r + 1) & 1] = 0;
             // A <- U^H A U in one pass from the old A into the other buffer:
             //   A'(a, b) = conj(U(a,a)) [A(a,b) U(b,b) + A(a,b') U(b',b)]
             //            + conj(U(a',a)) [A(a',b) U(b,b) + A(a',b') U(b',b)]
             // and V <- V U in place, a pair of columns per item
-            for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+            for (int e = threadIdx.x; any && e < k * k; e += blockDim.x) {
                 const int b = (int)(((unsigned)e * kinv) >> 20), a = e - b * k;
                 const int a2 = partner[a], b2 = partner[b];
                 const C ub = us[b], ub2 = up[b];
@@ -1010,7 +1036,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 const bool killed = b == a2 && a != b && (up[a].x != 0 || up[a].y != 0);
                 A2[e] = killed ? czero<C>() : cadd(cmulc(us[a], top), cmulc(up[a], bot));
             }
-            for (int e = threadIdx.x; e < (m / 2) * k; e += blockDim.x) {
+            for (int e = threadIdx.x; any && e < (m / 2) * k; e += blockDim.x) {
                 const int i = (int)(((unsigned)e * kinv) >> 20), row = e - i * k;
                 const int p = pr[i].x, q = pr[i].y;
                 if (q >= k) continue;
@@ -1021,19 +1047,21 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 V[q * k + row] = mk(sn * vp.x + cs * eq.x, sn * vp.y + cs * eq.y);
             }
             __syncthreads();
-            { C* t = A; A = A2; A2 = t; }
+            if (any) { C* t = A; A = A2; A2 = t; }
         }
         if (nrot == 0) break;          // a sweep without a rotation: converged
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < k; ++i) order[i] = i;
-        for (int i = 0; i < k; ++i) {
-            int best = i;
-            for (int j = i + 1; j < k; ++j)
-                if (A[order[j] * k + order[j]].x > A[order[best] * k + order[best]].x) best = j;
-            const int t = order[i]; order[i] = order[best]; order[best] = t;
+    // descending order of the eigenvalues (ties by index): index i goes to
+    // the position given by its rank
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const R di = jacobi_key(A[i * k + i].x);
+        int pos = 0;
+        for (int j = 0; j < k; ++j) {
+            const R dj = jacobi_key(A[j * k + j].x);
+            pos += (dj > di || (dj == di && j < i)) ? 1 : 0;
         }
+        order[pos] = i;
     }
     __syncthreads();
     C* Vo = Vall + (long long)blockIdx.x * k * k;
@@ -1046,7 +1074,9 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
 // The same Jacobi iteration with one warp per matrix (k <= 64) and several
 // matrices per CTA: lanes share the work of a round, __syncwarp orders it.
 #undef JACOBI_COUNT_ROTATION
+#undef JACOBI_MARK_ROUND
 #define JACOBI_COUNT_ROTATION ++nrw
+#define JACOBI_MARK_ROUND (rr = 1)
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ Vall, int k, int batch,
@@ -1085,19 +1115,31 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
     const R floor_abs = polish == 1 ? (R)1e-15 : (R)0;
     for (int sweep = 0; sweep < (polish == 1 ? 20 : 40); ++sweep) {
         R off = 0, tot = 0;
+        int need = 0;                   // some pair is above the rotation threshold
         for (int e = lane; e < k * k; e += 32) {
             const C a = A[e];
             const R v = a.x * a.x + a.y * a.y;
             tot += v;
-            if ((e % k) != (e / k)) off += v;
+            const int b = e / k, aa = e - b * k;
+            if (aa != b) {
+                off += v;
+                if (aa < b) {
+                    const R app = A[aa * k + aa].x, aqq = A[b * k + b].x, ac = sqrt(v);
+                    if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
+                        ac > floor_abs && ac > 0)
+                        need = 1;
+                }
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             tot += __shfl_xor_sync(0xffffffffu, tot, o);
         }
         if (!(off > tol * tot) || tot == 0) break;
+        if (!__any_sync(0xffffffffu, need)) break;   // no pair would rotate: converged
         int nrw = 0;
         for (int r = 0; r < m - 1; ++r) {
+            int rr = 0;
             for (int i = lane; i < m / 2; i += 32) {
                 int p, q;
                 if (i == 0) { p = m - 1; q = r; }
@@ -1113,6 +1155,7 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
                     if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
                         ac > floor_abs && ac > 0) {
                         JACOBI_COUNT_ROTATION;
+                        JACOBI_MARK_ROUND;
                         const R tau = (aqq - app) / (2 * ac);
                         const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
                         cs = (R)1 / sqrt((R)1 + t * t);
@@ -1124,6 +1167,8 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
                 rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
                 pr[i] = make_int2(p, q);
             }
+            // a round without a rotation leaves A and V as they are
+            if (!__any_sync(0xffffffffu, rr)) continue;
             __syncwarp();
             for (int e = lane; e < (m / 2) * k; e += 32) {
                 const int i = e / k, row = e - i * k;
@@ -1165,14 +1210,15 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
         if (!__any_sync(0xffffffffu, nrw)) break;    // a sweep without a rotation: converged
     }
 #undef JACOBI_COUNT_ROTATION
-    if (lane == 0) {
-        for (int i = 0; i < k; ++i) order[i] = i;
-        for (int i = 0; i < k; ++i) {
-            int best = i;
-            for (int j = i + 1; j < k; ++j)
-                if (A[order[j] * k + order[j]].x > A[order[best] * k + order[best]].x) best = j;
-            const int t = order[i]; order[i] = order[best]; order[best] = t;
+#undef JACOBI_MARK_ROUND
+    for (int i = lane; i < k; i += 32) {
+        const R di = jacobi_key(A[i * k + i].x);
+        int pos = 0;
+        for (int j = 0; j < k; ++j) {
+            const R dj = jacobi_key(A[j * k + j].x);
+            pos += (dj > di || (dj == di && j < i)) ? 1 : 0;
         }
+        order[pos] = i;
     }
     __syncwarp();
     C* Vo = Vall + (long long)mat * k * k;
@@ -1888,7 +1934,9 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
     }
     const size_t smb = sizeof(CT) * (3 * (size_t)k * k + 2 * (size_t)k) + sizeof(R) * 4 * (m / 2) +
                        sizeof(int2) * (m / 2) + sizeof(int) * (size_t)k;
-    k_heev_jacobi<R><<<batch, 256, smb, st>>>(G, V, k, polish);
+    // few matrices: the whole CTA of 1024 threads on each (a round is a
+    // handful of dependent steps; more threads make each one shorter)
+    k_heev_jacobi<R><<<batch, batch <= 2 * 152 ? 1024 : 256, smb, st>>>(G, V, k, polish);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }

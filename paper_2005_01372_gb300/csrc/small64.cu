@@ -26,6 +26,17 @@ namespace lsw {
 
 namespace {
 
+constexpr int GT_ROWS = 32;   // rows per tile (one compensated sum)
+constexpr int GT_MAXQ = 9;    // pairs per thread: 256 * 9 >= 64 * 65 / 2
+
+// Row chunks per block for the Gram and the product kernels: down to one
+// tile of 32 rows per CTA, about 1216 CTAs (8 per SM) over the batch, so
+// that a few small blocks (the recompressions on the inversion's critical
+// path) still spread over the GPU.
+int sketch_chunks(int m, int batch) {
+    return std::max(1, std::min((m + GT_ROWS - 1) / GT_ROWS, std::max(1, 1216 / batch)));
+}
+
 int grid_small(long long n, int bs = 256) {
     long long g = (n + bs - 1) / bs;
     return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 32));
@@ -54,8 +65,6 @@ __device__ __forceinline__ void tri_pair(int p, int& i, int& j) {
     i = p - jj * (jj + 1) / 2;
 }
 
-constexpr int GT_ROWS = 32;   // rows per tile (one compensated sum)
-constexpr int GT_MAXQ = 9;    // pairs per thread: 256 * 9 >= 64 * 65 / 2
 
 // Partial Gram of rows [r0, r1) of block b: part[(b * nchunk + ch) * npair + p]
 // for the upper-triangle pairs p.  Columns are staged in shared memory in
@@ -375,7 +384,7 @@ k_rmul_dot2(float2* __restrict__ Y, int m, int k, long long sY, const double2* _
 // computed, lower mirrored).  Small eigenvalues of G that FP32 could not
 // separate inside G (below ~1e-7 of the largest) sit on B's diagonal with
 // their own exponents, where an FP32 Jacobi resolves them.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(1024)
 k_rr_project(const double2* __restrict__ Gall, const float2* __restrict__ V0all, int k, double2* __restrict__ Ball) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int kk = k * k;
@@ -462,7 +471,7 @@ lsw_status gram64_c64(const float2* Y, int m, int k, long long sY, int batch, do
                       const int* active) {
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
-    const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
+    const int nchunk = sketch_chunks(m, batch);
     const int npair = k * (k + 1) / 2;
     DevBuf part;
     LSW_TRY(part.alloc(sizeof(double2) * (size_t)batch * nchunk * npair, st));
@@ -508,7 +517,10 @@ lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t 
         LSW_CUDA(cudaFuncSetAttribute(k_rr_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr.store(true);
     }
-    k_rr_project<<<batch, 128, sizeof(float2) * 5 * kk, st>>>(G, V0.as<float2>(), k, B.as<double2>());
+    // few matrices (the critical path of the recursive inversion): a CTA of
+    // 1024 threads on each
+    k_rr_project<<<batch, batch <= 2 * 152 ? 1024 : 128, sizeof(float2) * 5 * kk, st>>>(G, V0.as<float2>(), k,
+                                                                                       B.as<double2>());
     LSW_LAUNCH_CHECK();
     LSW_TRY(heev_jacobi<float>(B.as<double2>(), Z.as<float2>(), k, batch, st, 1));
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
@@ -551,7 +563,7 @@ lsw_status qr_sketch_c64(float2* A, int m, int k, long long sA, int batch, cudaS
         attr.store(true);
     }
     const size_t smp = sizeof(float2) * (2 * (size_t)k * k + (size_t)(GT_ROWS + 1) * k);
-    const int nchunk = std::max(1, std::min((m + 255) / 256, std::max(1, 1216 / batch)));
+    const int nchunk = sketch_chunks(m, batch);
     auto pass = [&](const int* active, int* need2) -> lsw_status {
         LSW_TRY(gram64_c64(A, m, k, sA, batch, G.as<double2>(), st, active));
         LSW_TRY(chol_rinv<double>(G.as<double2>(), k, batch, 0.0, Ri.as<double2>(), st, active, need2));
