@@ -907,15 +907,20 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     C* A = reinterpret_cast<C*>(sm_raw);        // k x k, column-major
     C* A2 = A + k * k;                          // the next round's A
     C* V = A2 + k * k;
-    C* us = V + k * k;                          // per index a: U(a, a)
-    C* up = us + k;                             // per index a: U(a', a), a' its partner
-    R* rot = reinterpret_cast<R*>(up + k);      // per pair: cs, sn, cos(phi), sin(phi)
+    R* rot = reinterpret_cast<R*>(V + k * k);   // per pair: cs, sn, cos(phi), sin(phi)
     int2* pr = reinterpret_cast<int2*>(rot + 4 * (m / 2));
-    int* partner = reinterpret_cast<int*>(pr + m / 2);
     __shared__ C red[33];
     __shared__ double trs;
     __shared__ int order[64];
     __shared__ int nrot;
+    // the 2 x 2 blocks (pair i, pair j), i <= j, of a round's update
+    __shared__ short2 blk[32 * 33 / 2];
+    const int nbt = (m / 2) * (m / 2 + 1) / 2;
+    for (int t = threadIdx.x; t < nbt; t += blockDim.x) {
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        blk[t] = make_short2((short)(t - j * (j + 1) / 2), (short)j);
+    }
     const double2* G = Gall + (long long)blockIdx.x * k * k;
     // e / k for e < k * k <= 4096 by a multiply and a shift (exact for k < 256)
     const unsigned kinv = (1u << 20) / (unsigned)k + 1u;
@@ -1002,49 +1007,68 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 }
                 rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
                 pr[i] = make_int2(p, q);
-                // U on (p, q): col p of U = cs e_p - sn e^{-i phi} e_q,
-                //              col q of U = sn e_p + cs e^{-i phi} e_q
-                const C em = mk(cp, -spp);
-                if (q < k) {
-                    us[p] = mk(cs, (R)0);
-                    up[p] = mk(-sn * em.x, -sn * em.y);
-                    partner[p] = q;
-                    us[q] = mk(cs * em.x, cs * em.y);
-                    up[q] = mk(sn, (R)0);
-                    partner[q] = p;
-                } else if (p < k) {
-                    us[p] = mk((R)1, (R)0);
-                    up[p] = czero<C>();
-                    partner[p] = p;
-                }
             }
             __syncthreads();
             // a round without a rotation leaves A and V as they are
             const bool any = rf[r & 1] != 0;
             if (threadIdx.x == 0) rf[(r + 1) & 1] = 0;
-            // A <- U^H A U in one pass from the old A into the other buffer:
-            //   A'(a, b) = conj(U(a,a)) [A(a,b) U(b,b) + A(a,b') U(b',b)]
-            //            + conj(U(a',a)) [A(a',b) U(b,b) + A(a',b') U(b',b)]
-            // and V <- V U in place, a pair of columns per item
-            for (int e = threadIdx.x; any && e < k * k; e += blockDim.x) {
-                const int b = (int)(((unsigned)e * kinv) >> 20), a = e - b * k;
-                const int a2 = partner[a], b2 = partner[b];
-                const C ub = us[b], ub2 = up[b];
-                const C top = cadd(cmul(A[b * k + a], ub), cmul(A[b2 * k + a], ub2));
-                const C bot = cadd(cmul(A[b * k + a2], ub), cmul(A[b2 * k + a2], ub2));
-                // the entry a rotation annihilates is zero by construction
-                const bool killed = b == a2 && a != b && (up[a].x != 0 || up[a].y != 0);
-                A2[e] = killed ? czero<C>() : cadd(cmulc(us[a], top), cmulc(up[a], bot));
-            }
-            for (int e = threadIdx.x; any && e < (m / 2) * k; e += blockDim.x) {
-                const int i = (int)(((unsigned)e * kinv) >> 20), row = e - i * k;
-                const int p = pr[i].x, q = pr[i].y;
-                if (q >= k) continue;
-                const R cs = rot[4 * i], sn = rot[4 * i + 1];
-                const C em = mk(rot[4 * i + 2], -rot[4 * i + 3]);   // e^{-i phi}
-                const C vp = V[p * k + row], eq = cmul(em, V[q * k + row]);
-                V[p * k + row] = mk(cs * vp.x - sn * eq.x, cs * vp.y - sn * eq.y);
-                V[q * k + row] = mk(sn * vp.x + cs * eq.x, sn * vp.y + cs * eq.y);
+            // U on pair (p, q): col p = cs e_p - sn e^{-i phi} e_q, col q = sn e_p
+            // + cs e^{-i phi} e_q, i.e. the 2 x 2 block J = [cs, sn; -sn em, cs em]
+            // (em = e^{-i phi}).  A <- U^H A U by 2 x 2 blocks, one item per
+            // pair of pairs i <= j from the old A into the other buffer:
+            //   A'[{p,q}, {p',q'}] = J_i^H A[{p,q}, {p',q'}] J_j,
+            // the block (j, i) its conjugate transpose; the index beyond k (odd
+            // k) has no row or column.  V <- V U in place, one row of a pair of
+            // columns per item.
+            const int nvt = (m / 2) * k;
+            for (int t = threadIdx.x; any && t < nbt + nvt; t += blockDim.x) {
+                if (t < nbt) {
+                    const short2 ij = blk[t];
+                    const int i = ij.x, j = ij.y;
+                    const int p = pr[i].x, q = pr[i].y, p2 = pr[j].x, q2 = pr[j].y;
+                    const bool hq = q < k, hq2 = q2 < k;
+                    const R c1 = rot[4 * i], s1 = rot[4 * i + 1], c2 = rot[4 * j], s2 = rot[4 * j + 1];
+                    const C ep1 = mk(rot[4 * i + 2], rot[4 * i + 3]);    // conj(em) of pair i
+                    const C em2 = mk(rot[4 * j + 2], -rot[4 * j + 3]);   // em of pair j
+                    const C b00 = A[p2 * k + p];
+                    const C b01 = hq2 ? A[q2 * k + p] : czero<C>();
+                    const C b10 = hq ? A[p2 * k + q] : czero<C>();
+                    const C b11 = (hq && hq2) ? A[q2 * k + q] : czero<C>();
+                    // T = J_i^H B:  row p: cs b0x - sn ep b1x,  row q: sn b0x + cs ep b1x
+                    const C e10 = cmul(ep1, b10), e11 = cmul(ep1, b11);
+                    const C t00 = mk(c1 * b00.x - s1 * e10.x, c1 * b00.y - s1 * e10.y);
+                    const C t01 = mk(c1 * b01.x - s1 * e11.x, c1 * b01.y - s1 * e11.y);
+                    const C t10 = mk(s1 * b00.x + c1 * e10.x, s1 * b00.y + c1 * e10.y);
+                    const C t11 = mk(s1 * b01.x + c1 * e11.x, s1 * b01.y + c1 * e11.y);
+                    // B' = T J_j:  col p': cs' Tx0 - sn' em' Tx1,  col q': sn' Tx0 + cs' em' Tx1
+                    const C f01 = cmul(t01, em2), f11 = cmul(t11, em2);
+                    C n00 = mk(c2 * t00.x - s2 * f01.x, c2 * t00.y - s2 * f01.y);
+                    C n01 = mk(s2 * t00.x + c2 * f01.x, s2 * t00.y + c2 * f01.y);
+                    C n10 = mk(c2 * t10.x - s2 * f11.x, c2 * t10.y - s2 * f11.y);
+                    C n11 = mk(s2 * t10.x + c2 * f11.x, s2 * t10.y + c2 * f11.y);
+                    if (i == j) {
+                        // the diagonal block: the entry the rotation annihilates is zero
+                        if (s1 != (R)0) { n01 = czero<C>(); n10 = czero<C>(); }
+                        A2[p * k + p] = n00;
+                        if (hq) { A2[q * k + p] = n01; A2[p * k + q] = n10; A2[q * k + q] = n11; }
+                    } else {
+                        A2[p2 * k + p] = n00;
+                        A2[p * k + p2] = cconj(n00);
+                        if (hq2) { A2[q2 * k + p] = n01; A2[p * k + q2] = cconj(n01); }
+                        if (hq) { A2[p2 * k + q] = n10; A2[q * k + p2] = cconj(n10); }
+                        if (hq && hq2) { A2[q2 * k + q] = n11; A2[q * k + q2] = cconj(n11); }
+                    }
+                } else {
+                    const int e = t - nbt;
+                    const int i = (int)(((unsigned)e * kinv) >> 20), row = e - i * k;
+                    const int p = pr[i].x, q = pr[i].y;
+                    if (q >= k) continue;
+                    const R cs = rot[4 * i], sn = rot[4 * i + 1];
+                    const C em = mk(rot[4 * i + 2], -rot[4 * i + 3]);   // e^{-i phi}
+                    const C vp = V[p * k + row], eq = cmul(em, V[q * k + row]);
+                    V[p * k + row] = mk(cs * vp.x - sn * eq.x, cs * vp.y - sn * eq.y);
+                    V[q * k + row] = mk(sn * vp.x + cs * eq.x, sn * vp.y + cs * eq.y);
+                }
             }
             __syncthreads();
             if (any) { C* t = A; A = A2; A2 = t; }
@@ -1932,8 +1956,7 @@ lsw_status heev_jacobi(const double2* G, typename Cx<R>::T* V, int k, int batch,
         LSW_CUDA(cudaFuncSetAttribute(k_heev_jacobi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
         attrb[sizeof(R) == 8] = true;
     }
-    const size_t smb = sizeof(CT) * (3 * (size_t)k * k + 2 * (size_t)k) + sizeof(R) * 4 * (m / 2) +
-                       sizeof(int2) * (m / 2) + sizeof(int) * (size_t)k;
+    const size_t smb = sizeof(CT) * 3 * (size_t)k * k + sizeof(R) * 4 * (m / 2) + sizeof(int2) * (m / 2);
     // few matrices: the whole CTA of 1024 threads on each (a round is a
     // handful of dependent steps; more threads make each one shorter)
     k_heev_jacobi<R><<<batch, batch <= 2 * 152 ? 1024 : 256, smb, st>>>(G, V, k, polish);

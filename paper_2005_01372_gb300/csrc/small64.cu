@@ -159,14 +159,17 @@ __global__ void k_gram_c64_reduce(const double2* __restrict__ part, int nchunk, 
 }
 
 // ------------------------------------------- Cholesky and R^-1 (FP64)
-// One CTA per matrix: G + shift I = L L^H (L = R^H lower triangular), then
-// X = L^-1 and Rinv = R^-1 = X^H.  Written for the latency and rate of FP64
-// on this GPU: every pivot's reciprocal square root comes from an FP32
-// estimate and two Newton steps (no FP64 division or square root on the
-// chain), the trailing update and the substitution are independent
-// multiply-adds spread over four warps (the four FP64 units of an SM), and
-// the substitution runs in axpy form for all columns at once, so a step
-// waits on one multiply-add, not on a dot product.
+// One CTA per matrix: G + shift I = Lt D Lt^H (Lt unit lower triangular, D
+// diagonal: the square-root-free Cholesky), then Xt = Lt^-1 and
+// R^-1 = Xt^H D^-1/2 (R = D^1/2 Lt^H, so R^H R = G + shift I).
+// Written for the rate and latency of FP64 on this GPU (2 FP64 lanes per
+// cycle per SM): every multiply-add a thread issues is useful (the trailing
+// triangle is enumerated through a table, not masked out of a square), a
+// step waits on one barrier-separated phase of independent multiply-adds,
+// the pivot's reciprocal (an FP32 estimate and two Newton steps, no FP64
+// division) is formed by the thread that finishes the pivot while the
+// others finish the step, and the square roots of D are taken once, at the
+// end, for all columns at once.
 // A non-positive pivot restarts the factorisation with a larger shift
 // (1e-15 tr(G) / k, then x100, at most 12 times).  A block with tr(G) = 0
 // gets Rinv = 0 (its Q is zero, which the truncation keeps as a zero block).
@@ -181,32 +184,56 @@ __device__ __forceinline__ double rsqrt64(double d) {
     return y;
 }
 
+__device__ __forceinline__ double rcp64(double d) {
+    float f = (float)d;
+    double y = (f > 1e-37f && f < 1e37f) ? (double)(1.0f / f) : 1.0 / d;
+    // y <- y (2 - d y), twice
+    for (int it = 0; it < 2; ++it) {
+        const double e = fma(-d, y, 1.0);
+        y = fma(y, e, y);
+    }
+    return y;
+}
+
+constexpr int CH_NT = 256;   // threads per matrix
+
 template <typename C>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(CH_NT)
 k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel, C* __restrict__ Rall,
             const int* __restrict__ active, int* __restrict__ need2) {
-    // one CTA (four warps, one per SM sub-partition and its FP64 unit) per matrix
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int tid = threadIdx.x, NT = blockDim.x;
+    const int tid = threadIdx.x;
     const int mat = blockIdx.x;
     if (active && !active[mat]) return;
     const int ld = k + 1;
-    double2* L = reinterpret_cast<double2*>(sm_raw);
-    double2* X = L + (size_t)k * ld;
-    double* rinv = reinterpret_cast<double*>(X + (size_t)k * ld);
-    __shared__ double red[4];
+    // A: lower triangle = the matrix being factored (then Lt D), upper
+    // triangle = U(j, l) = conj(Lt(l, j)), written as each column finishes
+    double2* A = reinterpret_cast<double2*>(sm_raw);
+    double2* X = A + (size_t)k * ld;                            // Xt = Lt^-1, lower
+    double* dinv = reinterpret_cast<double*>(X + (size_t)k * ld);  // 1 / D(j)
+    short2* tri = reinterpret_cast<short2*>(dinv + k);          // p -> (a, b), a <= b
+    __shared__ double red[CH_NT / 32];
     __shared__ int fail;
     const double2* G = Gall + (long long)mat * k * k;
     C* Rout = Rall + (long long)mat * k * k;
+    const int ntri = k * (k - 1) / 2;
+    for (int p = tid; p < ntri; p += CH_NT) {
+        int bb = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+        while ((bb + 1) * (bb + 2) / 2 <= p) ++bb;
+        while (bb * (bb + 1) / 2 > p) --bb;
+        tri[p] = make_short2((short)(p - bb * (bb + 1) / 2), (short)bb);
+    }
     double tr = 0.0;
-    for (int i = tid; i < k; i += NT) tr += G[i * k + i].x;
+    for (int i = tid; i < k; i += CH_NT) tr += G[i * k + i].x;
     for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
     if ((tid & 31) == 0) red[tid >> 5] = tr;
     __syncthreads();
-    tr = (red[0] + red[1] + red[2] + red[3]) / k;
+    tr = 0.0;
+    for (int w = 0; w < CH_NT / 32; ++w) tr += red[w];
+    tr /= k;
     if (!(tr > 0.0) || !isfinite(tr)) {
         const double fill = (tr == 0.0) ? 0.0 : NAN;
-        for (int e = tid; e < k * k; e += NT) { Rout[e].x = fill; Rout[e].y = fill; }
+        for (int e = tid; e < k * k; e += CH_NT) { Rout[e].x = fill; Rout[e].y = fill; }
         if (need2 && tid == 0) need2[mat] = 0;
         return;
     }
@@ -215,92 +242,98 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
     int attempts = 0;
     bool ok = false;
     for (int attempt = 0; attempt < 13 && !ok; ++attempt) {
-        for (int e = tid; e < k * k; e += NT) {
+        for (int e = tid; e < k * k; e += CH_NT) {
             const int j = e / k, i = e - j * k;
+            if (i < j) continue;
             double2 v = G[e];
             if (i == j) { v.x += shift; v.y = 0.0; }
-            L[j * ld + i] = v;
+            A[j * ld + i] = v;
         }
-        if (tid == 0) fail = 0;
-        __syncthreads();
-        for (int j = 0; j < k; ++j) {
-            const double djj = L[j * ld + j].x;
-            if (!(djj > 0.0) || !isfinite(djj)) {    // uniform: every thread reads the same pivot
-                if (tid == 0) fail = 1;
-                break;
-            }
-            const double r = rsqrt64(djj);
-            __syncthreads();
-            for (int i = j + 1 + tid; i < k; i += NT) {
-                const double2 v = L[j * ld + i];
-                L[j * ld + i] = make_double2(v.x * r, v.y * r);
-            }
-            if (tid == 0) {
-                L[j * ld + j] = make_double2(djj * r, 0.0);
-                rinv[j] = r;
-            }
-            __syncthreads();
-            // trailing lower triangle: L(i, l) -= L(i, j) conj(L(l, j)), j < l <= i
-            const int nt = k - 1 - j;
-            for (int e = tid; e < nt * nt; e += NT) {
-                const int ll = e / nt, ii = e - ll * nt;
-                if (ii < ll) continue;
-                const int i = j + 1 + ii, l = j + 1 + ll;
-                const double2 a = L[j * ld + i], bq = L[j * ld + l];
-                double2 v = L[l * ld + i];
-                v.x -= a.x * bq.x + a.y * bq.y;
-                v.y -= a.y * bq.x - a.x * bq.y;
-                L[l * ld + i] = v;
-            }
-            __syncthreads();
+        if (tid == 0) {
+            const double d0 = G[0].x + shift;
+            fail = (d0 > 0.0 && isfinite(d0)) ? 0 : 1;
+            dinv[0] = rcp64(d0);
         }
         __syncthreads();
+        for (int j = 0; j < k - 1 && !fail; ++j) {
+            // column j of Lt, kept conjugated in row j: U(j, i) = conj(A(i, j)) / D(j)
+            const double dj = dinv[j];
+            for (int i = j + 1 + tid; i < k; i += CH_NT) {
+                const double2 v = A[j * ld + i];
+                A[i * ld + j] = make_double2(v.x * dj, -v.y * dj);
+            }
+            __syncthreads();
+            // trailing triangle: A(i, l) -= A(i, j) U(j, l), j < l <= i; item
+            // 0 (the next pivot) first, on thread 0, which then forms 1 / D(j+1)
+            const int nt = k - 1 - j, T = nt * (nt + 1) / 2;
+            for (int p = tid; p < T; p += CH_NT) {
+                const short2 ab = tri[T - 1 - p];
+                const int i = j + nt - ab.x, l = j + nt - ab.y;
+                const double2 a = A[j * ld + i], u = A[l * ld + j];
+                double2 v = A[l * ld + i];
+                v.x = fma(-a.x, u.x, v.x);
+                v.x = fma(a.y, u.y, v.x);
+                v.y = fma(-a.x, u.y, v.y);
+                v.y = fma(-a.y, u.x, v.y);
+                A[l * ld + i] = v;
+                if (p == 0) {
+                    const double d = v.x;
+                    if (!(d > 0.0) || !isfinite(d)) fail = 1;
+                    dinv[j + 1] = rcp64(d);
+                }
+            }
+            __syncthreads();
+        }
         ok = fail == 0;
         __syncthreads();
         if (!ok) shift = shift > 0.0 ? shift * 100.0 : 1e-15 * tr;
         ++attempts;
     }
     if (!ok) {
-        for (int e = tid; e < k * k; e += NT) { Rout[e].x = NAN; Rout[e].y = NAN; }
+        for (int e = tid; e < k * k; e += CH_NT) { Rout[e].x = NAN; Rout[e].y = NAN; }
         if (need2 && tid == 0) need2[mat] = 0;
         return;
     }
-    // X = L^-1 in axpy form, every column at once: X starts as I; step t
-    // fixes row t (x_t = b_t / L(t, t) in each column c <= t) and removes it
-    // from the rows below: b_i -= L(i, t) x_t.
-    for (int e = tid; e < k * ld; e += NT) {
+    // Xt = Lt^-1 in axpy form, every column at once: Xt starts as I; after
+    // step t - 1 row t is final in every column c <= t, and step t removes it
+    // from the rows below: Xt(i, c) -= Lt(i, t) Xt(t, c), Lt(i, t) = conj(U(t, i)).
+    for (int e = tid; e < k * ld; e += CH_NT) {
         const int c = e / ld, i = e - c * ld;
         X[e] = make_double2(i == c ? 1.0 : 0.0, 0.0);
     }
     __syncthreads();
-    for (int t = 0; t < k; ++t) {
-        const double rt = rinv[t];
-        for (int c = tid; c <= t; c += NT) {
-            const double2 bt = X[c * ld + t];
-            X[c * ld + t] = make_double2(bt.x * rt, bt.y * rt);
-        }
-        __syncthreads();
-        const int nr = k - 1 - t, nc = t + 1;
-        for (int e = tid; e < nr * nc; e += NT) {
-            const int c = e / nr, i = t + 1 + (e - c * nr);
-            const double2 a = L[t * ld + i], xt = X[c * ld + t];
+    for (int t = 0; t < k - 1; ++t) {
+        const int nr = k - 1 - t, n = nr * (t + 1);
+        const float rnr = 1.0f / (float)nr;
+        for (int e = tid; e < n; e += CH_NT) {
+            // e = c * nr + (i - t - 1); the float quotient is exact here
+            // (e < 4096, nr < 64: the fraction is at least 1 / (2 nr) from an integer)
+            const int c = (int)(((float)e + 0.5f) * rnr), i = t + 1 + (e - c * nr);
+            const double2 u = A[i * ld + t], xt = X[c * ld + t];
             double2 v = X[c * ld + i];
-            v.x -= a.x * xt.x - a.y * xt.y;
-            v.y -= a.x * xt.y + a.y * xt.x;
+            // v -= conj(u) xt
+            v.x = fma(-u.x, xt.x, v.x);
+            v.x = fma(-u.y, xt.y, v.x);
+            v.y = fma(-u.x, xt.y, v.y);
+            v.y = fma(u.y, xt.x, v.y);
             X[c * ld + i] = v;
         }
         __syncthreads();
     }
-    // Rinv(i, j) = conj(X(j, i)), upper triangular
+    // D^-1/2 for every column at once (reuses dinv)
+    for (int j = tid; j < k; j += CH_NT) dinv[j] = rsqrt64(A[j * ld + j].x);
+    __syncthreads();
+    // Rinv(i, j) = conj(Xt(j, i)) D(j)^-1/2, upper triangular
     double fro = 0.0;
-    for (int e = tid; e < k * k; e += NT) {
+    for (int e = tid; e < k * k; e += CH_NT) {
         const int j = e / k, i = e - j * k;
         C v;
         if (i <= j) {
             const double2 xv = X[i * ld + j];
-            v.x = xv.x;
-            v.y = -xv.y;
-            fro += xv.x * xv.x + xv.y * xv.y;
+            const double s = dinv[j];
+            v.x = xv.x * s;
+            v.y = -xv.y * s;
+            fro += (double)v.x * v.x + (double)v.y * v.y;
         } else {
             v.x = 0;
             v.y = 0;
@@ -317,7 +350,8 @@ k_chol_rinv(const double2* __restrict__ Gall, int k, int batch, double shift_rel
         if ((tid & 31) == 0) red[tid >> 5] = fro;
         __syncthreads();
         if (tid == 0) {
-            const double rf = red[0] + red[1] + red[2] + red[3];
+            double rf = 0.0;
+            for (int w = 0; w < CH_NT / 32; ++w) rf += red[w];
             const double kap2 = tr * k * rf;
             need2[mat] = (shifted0 || attempts > 0 || !(kap2 <= 1e6)) ? 1 : 0;
         }
@@ -490,14 +524,15 @@ lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typen
     typedef typename Cx<R>::T C;
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
-    const size_t per = sizeof(double2) * (2 * (size_t)k * (k + 1) + k);
+    const size_t per = sizeof(double2) * 2 * (size_t)k * (k + 1) + sizeof(double) * k +
+                       sizeof(short2) * (size_t)(k * (k - 1) / 2 + 1);
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         LSW_CUDA(cudaFuncSetAttribute(k_chol_rinv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr.store(true);
     }
     KTimer kt("chol", st, 0.0, 0.0);
-    k_chol_rinv<C><<<batch, 128, per, st>>>(G, k, batch, shift_rel, Rinv, active, need2);
+    k_chol_rinv<C><<<batch, CH_NT, per, st>>>(G, k, batch, shift_rel, Rinv, active, need2);
     LSW_LAUNCH_CHECK();
     return LSW_OK;
 }
