@@ -115,19 +115,23 @@ template <typename R> struct HStore {
     }
 };
 
-// Low-rank updates that the inversion adds to the dense leaves of the matrix
-// being inverted (the Schur complements S = D - C A^-1 B), kept as factors:
-// leaf c accumulates U_c V_c^H with r columns per ancestor whose right
-// subtree holds it, stored left to right in the order they arrive.
+// The dense leaves of the matrix being inverted hold their inverses: the
+// original leaves are inverted up front, in batches on another stream
+// (leaves [end[b-1], end[b]) are ready once ready[b] has fired), and every
+// rank-r update D += U V^H that a Schur complement S = D - C A^-1 B brings
+// to a leaf is folded into its inverse at once by Woodbury.
 template <typename R> struct LeafUpd {
-    typedef typename Cx<R>::T C;
-    C* U = nullptr;   // nleaf x nL x kmax
-    C* V = nullptr;
-    int nL = 0, kmax = 0;
-    // the original leaves' inverses arrive in batches on another stream:
-    // leaves [end[b-1], end[b]) are ready once ready[b] has fired
     std::vector<cudaEvent_t> ready;
     std::vector<int> end;
+    // make st wait until every leaf up to `last` has its inverse
+    lsw_status wait(int last, cudaStream_t st) const {
+        for (size_t b = 0; b < end.size(); ++b)
+            if (last < end[b]) {
+                LSW_CUDA(cudaStreamWaitEvent(st, ready[b], 0));
+                break;
+            }
+        return LSW_OK;
+    }
 };
 
 // H kept as BF16 pairs (re, im in one 32-bit word) after an FP32 build;
@@ -280,26 +284,12 @@ __global__ void k_concat(const C* __restrict__ U, const C* __restrict__ W, const
     }
 }
 
-// Leaves first..first+nleaf-1 receive X Y^H as factor columns [off, off + r).
+// M_b += I for a batch of r x r matrices (stride r * r).
 template <typename C>
-__global__ void k_leaf_append(const C* __restrict__ X, const C* __restrict__ Y, int m, int r, int nL, int nleaf,
-                              int first, int off, int kmax, C* __restrict__ U, C* __restrict__ V) {
-    const long long tot = (long long)nleaf * nL * r;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-        const int lf = (int)(e / ((long long)nL * r));
-        const long long q = e - (long long)lf * nL * r;
-        const int col = (int)(q / nL), i = (int)(q - (long long)col * nL);
-        const long long dst = ((long long)(first + lf) * kmax + off + col) * nL + i;
-        U[dst] = X[(long long)col * m + (long long)lf * nL + i];
-        V[dst] = Y[(long long)col * m + (long long)lf * nL + i];
-    }
-}
-
-template <typename C>
-__global__ void k_eye_plus(C* M, int r) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
-        const int j = e / r, i = e - j * r;
-        if (i == j) M[e].x += 1;
+__global__ void k_eye_plus(C* M, int r, int batch) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * batch; e += gridDim.x * blockDim.x) {
+        const int b = e / r, i = e - b * r;
+        M[(long long)b * r * r + (long long)i * r + i].x += 1;
     }
 }
 
@@ -809,12 +799,32 @@ lsw_status add_lowrank(HStore<R>& M, int l, int c, const typename Cx<R>::T* X, c
     const int rp = r + oversample;
     const int nleaf = 1 << (L - l);
     if (lu) {
-        // deferred: the leaves keep their inverses, the update goes to the
-        // factor lists, at the offset given by the right turns above call_l
-        const int off = r * __builtin_popcount((unsigned)call_c);
-        k_leaf_append<C><<<gridn((long long)nleaf * nL * r), 256, 0, st>>>(X, Y, m, r, nL, nleaf, c * nleaf, off,
-                                                                          lu->kmax, lu->U, lu->V);
+        // the leaves hold inverses: each leaf j of the node gets
+        // D_j^-1 <- (D_j + U_j V_j^H)^-1 with U_j, V_j its rows of X, Y, by
+        // Woodbury, batched over the node's leaves:
+        //   D^-1 - (D^-1 U) (I + V^H D^-1 U)^-1 (V^H D^-1)
+        KTimer kt_leaf("hodlr_leaf_woodbury", st, 0, 0);
+        LSW_TRY(lu->wait(c * nleaf + nleaf - 1, st));
+        C* D0 = M.D + (size_t)c * nleaf * nL * nL;
+        const long long nn = (long long)nL * nL, nr = (long long)nL * r;
+        DevBuf T1, T2, T3, Mc;
+        LSW_TRY(T1.alloc(sizeof(C) * (size_t)nleaf * nr, st));
+        LSW_TRY(T2.alloc(sizeof(C) * (size_t)nleaf * nr, st));
+        LSW_TRY(T3.alloc(sizeof(C) * (size_t)nleaf * nr, st));
+        LSW_TRY(Mc.alloc(sizeof(C) * (size_t)nleaf * r * r, st));
+        // T1 = D^-1 U, T2 = V^H D^-1, Mc = I + V^H T1
+        LSW_TRY(gemm<R>('N', 'N', nL, r, nL, one<C>(), D0, nL, nn, X, m, nL, zero<C>(), T1.as<C>(), nL, nr, nleaf, st));
+        LSW_TRY(gemm<R>('C', 'N', r, nL, nL, one<C>(), Y, m, nL, D0, nL, nn, zero<C>(), T2.as<C>(), r, nr, nleaf, st));
+        LSW_TRY(gemm<R>('C', 'N', r, r, nL, one<C>(), Y, m, nL, T1.as<C>(), nL, nr, zero<C>(), Mc.as<C>(), r,
+                        (long long)r * r, nleaf, st));
+        k_eye_plus<C><<<gridn((long long)r * nleaf), 256, 0, st>>>(Mc.as<C>(), r, nleaf);
         LSW_LAUNCH_CHECK();
+        LSW_TRY(inverse_gj<R>(Mc.as<C>(), r, (long long)r * r, nleaf, st));
+        // T3 = Mc^-1 T2, D^-1 -= T1 T3
+        LSW_TRY(gemm<R>('N', 'N', r, nL, r, one<C>(), Mc.as<C>(), r, (long long)r * r, T2.as<C>(), r, nr, zero<C>(),
+                        T3.as<C>(), r, nr, nleaf, st));
+        LSW_TRY(gemm<R>('N', 'N', nL, nL, r, minus_one<C>(), T1.as<C>(), nL, nr, T3.as<C>(), r, nr, one<C>(), D0, nL, nn,
+                        nleaf, st));
     } else {
         C* D0 = M.D + (size_t)c * nleaf * nL * nL;
         LSW_TRY(gemm<R>('N', 'C', nL, nL, r, one<C>(), X, m, nL, Y, m, nL, one<C>(), D0, nL, (long long)nL * nL, nleaf,
@@ -871,40 +881,14 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
     typedef typename Cx<R>::T C;
     const int L = X.L, r = X.r;
     if (l == L) {
-        // X's leaf holds D^-1 (all original leaves are inverted together up
-        // front); the leaf to invert is S = D + U V^H with the k = r popcount(c)
-        // update columns its ancestors appended, so by Woodbury
-        //   S^-1 = D^-1 - D^-1 U (I + V^H D^-1 U)^-1 V^H D^-1.
+        // X's leaf already holds the inverse of the leaf to invert (the
+        // original leaf's inverse with every update of its ancestors' Schur
+        // complements folded in)
         const int nL = X.nl(L);
         const long long nn = (long long)nL * nL;
-        for (size_t b = 0; b < lu.end.size(); ++b)
-            if (c < lu.end[b]) {
-                LSW_CUDA(cudaStreamWaitEvent(st, lu.ready[b], 0));
-                break;
-            }
-        KTimer kt_leaf("hodlr_leaf_woodbury", st, 0, 0);
-        const C* Di = X.D + (size_t)c * nn;
-        C* d = Hi.D + (size_t)c * nn;
-        LSW_CUDA(cudaMemcpyAsync(d, Di, sizeof(C) * nn, cudaMemcpyDeviceToDevice, st));
-        const int k = r * __builtin_popcount((unsigned)c);
-        if (k == 0) return LSW_OK;
-        const C* U = lu.U + (size_t)c * lu.kmax * nL;
-        const C* V = lu.V + (size_t)c * lu.kmax * nL;
-        DevBuf T1, T2, T3, M;
-        LSW_TRY(T1.alloc(sizeof(C) * (size_t)nL * k, st));
-        LSW_TRY(T2.alloc(sizeof(C) * (size_t)nL * k, st));
-        LSW_TRY(T3.alloc(sizeof(C) * (size_t)nL * k, st));
-        LSW_TRY(M.alloc(sizeof(C) * (size_t)k * k, st));
-        LSW_TRY(gemm<R>('N', 'N', nL, k, nL, one<C>(), Di, nL, 0, U, nL, 0, zero<C>(), T1.as<C>(), nL, 0, 1, st));
-        LSW_TRY(gemm<R>('C', 'N', k, k, nL, one<C>(), V, nL, 0, T1.as<C>(), nL, 0, zero<C>(), M.as<C>(), k, 0, 1, st));
-        k_eye_plus<C><<<gridn((long long)k * k), 256, 0, st>>>(M.as<C>(), k);
-        LSW_LAUNCH_CHECK();
-        LSW_TRY(inverse_gj<R>(M.as<C>(), k, (long long)k * k, 1, st));
-        LSW_TRY(gemm<R>('C', 'N', k, nL, nL, one<C>(), V, nL, 0, Di, nL, 0, zero<C>(), T2.as<C>(), k, 0, 1, st));
-        LSW_TRY(gemm<R>('N', 'N', k, nL, k, one<C>(), M.as<C>(), k, 0, T2.as<C>(), k, 0, zero<C>(), T3.as<C>(), k, 0, 1,
-                        st));
-        LSW_TRY(gemm<R>('N', 'N', nL, nL, k, minus_one<C>(), T1.as<C>(), nL, 0, T3.as<C>(), k, 0, one<C>(), d, nL, 0, 1,
-                        st));
+        LSW_TRY(lu.wait(c, st));
+        LSW_CUDA(cudaMemcpyAsync(Hi.D + (size_t)c * nn, X.D + (size_t)c * nn, sizeof(C) * nn, cudaMemcpyDeviceToDevice,
+                                 st));
         return LSW_OK;
     }
     const int a = 2 * c, b = 2 * c + 1, m1 = X.nl(l + 1);
@@ -1023,16 +1007,6 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
         LSW_TRY(fk.join());
     }
     KTimer kti("hodlr_invert", st, 0, 0);
-    lu.nL = nL;
-    lu.kmax = std::max(1, r * L);
-    DevBuf ub, vb;
-    const size_t lub = sizeof(C) * (size_t)(1 << L) * nL * lu.kmax;
-    LSW_TRY(ub.alloc(lub, st));
-    LSW_TRY(vb.alloc(lub, st));
-    LSW_CUDA(cudaMemsetAsync(ub.p, 0, lub, st));
-    LSW_CUDA(cudaMemsetAsync(vb.p, 0, lub, st));
-    lu.U = ub.as<C>();
-    lu.V = vb.as<C>();
     LSW_TRY(Hi.alloc(L, r, tr.n));
     LSW_TRY(invert_node<R>(X, 0, 0, Hi, hp->oversample, hp->seed, st, lu));
     LSW_TRY(fkd.join());

@@ -896,7 +896,6 @@ template <typename R> __device__ __forceinline__ R jacobi_skip() { return sizeof
 template <typename R>
 __device__ __forceinline__ R jacobi_key(R d) { return isnan(d) ? -INFINITY : d; }
 
-#define JACOBI_COUNT_ROTATION atomicAdd(&nrot, 1)
 #define JACOBI_MARK_ROUND (rf[r & 1] = 1)
 template <typename R>
 __global__ void __launch_bounds__(1024)
@@ -924,6 +923,7 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
     const double2* G = Gall + (long long)blockIdx.x * k * k;
     // e / k for e < k * k <= 4096 by a multiply and a shift (exact for k < 256)
     const unsigned kinv = (1u << 20) / (unsigned)k + 1u;
+    const unsigned khinv = (1u << 20) / (unsigned)((k + 1) >> 1) + 1u;
     if (threadIdx.x < 32) {
         double t = 0;
         for (int i = threadIdx.x; i < k; i += 32) t += fabs(G[i * k + i].x);
@@ -990,19 +990,22 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                 if (q < k) {
                     const R app = A[p * k + p].x, aqq = A[q * k + q].x;
                     const C c = A[q * k + p];   // A[p][q]
-                    const R ac = sqrt(c.x * c.x + c.y * c.y);
+                    const R ac2 = c.x * c.x + c.y * c.y, ac = sqrt(ac2);
                     // rotate only while the pair is not yet negligible
                     // against its diagonal (relative threshold above rounding)
                     if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
                         ac > floor_abs && ac > 0) {
-                        JACOBI_COUNT_ROTATION;
+                        nrot = 1;
                         JACOBI_MARK_ROUND;
-                        const R tau = (aqq - app) / (2 * ac);
-                        const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+                        // t = tan(theta) = sign(d) 2|a_pq| / (|d| + sqrt(d^2 + 4|a_pq|^2)),
+                        // d = a_qq - a_pp: the smaller root of t^2 + (d / |a_pq|) t - 1 = 0
+                        const R d = aqq - app;
+                        const R t = (d >= 0 ? (R)2 : (R)-2) * ac / (fabs(d) + sqrt(d * d + 4 * ac2));
+                        const R rac = (R)1 / ac;
                         cs = (R)1 / sqrt((R)1 + t * t);
                         sn = t * cs;
-                        cp = c.x / ac;
-                        spp = c.y / ac;
+                        cp = c.x * rac;
+                        spp = c.y * rac;
                     }
                 }
                 rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
@@ -1020,7 +1023,8 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
             // the block (j, i) its conjugate transpose; the index beyond k (odd
             // k) has no row or column.  V <- V U in place, one row of a pair of
             // columns per item.
-            const int nvt = (m / 2) * k;
+            const int kh = (k + 1) >> 1;                    // row pairs of V
+            const int nvt = (m / 2) * kh;
             for (int t = threadIdx.x; any && t < nbt + nvt; t += blockDim.x) {
                 if (t < nbt) {
                     const short2 ij = blk[t];
@@ -1060,14 +1064,20 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
                     }
                 } else {
                     const int e = t - nbt;
-                    const int i = (int)(((unsigned)e * kinv) >> 20), row = e - i * k;
+                    const int i = (int)(((unsigned)e * khinv) >> 20), r0 = 2 * (e - i * kh);
                     const int p = pr[i].x, q = pr[i].y;
                     if (q >= k) continue;
                     const R cs = rot[4 * i], sn = rot[4 * i + 1];
                     const C em = mk(rot[4 * i + 2], -rot[4 * i + 3]);   // e^{-i phi}
-                    const C vp = V[p * k + row], eq = cmul(em, V[q * k + row]);
-                    V[p * k + row] = mk(cs * vp.x - sn * eq.x, cs * vp.y - sn * eq.y);
-                    V[q * k + row] = mk(sn * vp.x + cs * eq.x, sn * vp.y + cs * eq.y);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int row = r0 + u;
+                        if (row < k) {
+                            const C vp = V[p * k + row], eq = cmul(em, V[q * k + row]);
+                            V[p * k + row] = mk(cs * vp.x - sn * eq.x, cs * vp.y - sn * eq.y);
+                            V[q * k + row] = mk(sn * vp.x + cs * eq.x, sn * vp.y + cs * eq.y);
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -1097,7 +1107,6 @@ k_heev_jacobi(const double2* __restrict__ Gall, typename Cx<R>::T* __restrict__ 
 
 // The same Jacobi iteration with one warp per matrix (k <= 64) and several
 // matrices per CTA: lanes share the work of a round, __syncwarp orders it.
-#undef JACOBI_COUNT_ROTATION
 #undef JACOBI_MARK_ROUND
 #define JACOBI_COUNT_ROTATION ++nrw
 #define JACOBI_MARK_ROUND (rr = 1)
@@ -1173,19 +1182,21 @@ k_heev_jacobi_warp(const double2* __restrict__ Gall, typename Cx<R>::T* __restri
                 if (q < k) {
                     const R app = A[p * k + p].x, aqq = A[q * k + q].x;
                     const C c = A[q * k + p];
-                    const R ac = sqrt(c.x * c.x + c.y * c.y);
+                    const R ac2 = c.x * c.x + c.y * c.y, ac = sqrt(ac2);
                     // rotate only while the pair is not yet negligible
                     // against its diagonal (relative threshold above rounding)
                     if (ac > skip * sqrt(fabs(app * aqq)) && ac > (R)1e-30 * (fabs(app) + fabs(aqq)) &&
                         ac > floor_abs && ac > 0) {
                         JACOBI_COUNT_ROTATION;
                         JACOBI_MARK_ROUND;
-                        const R tau = (aqq - app) / (2 * ac);
-                        const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+                        // the same rotation as the CTA version
+                        const R d = aqq - app;
+                        const R t = (d >= 0 ? (R)2 : (R)-2) * ac / (fabs(d) + sqrt(d * d + 4 * ac2));
+                        const R rac = (R)1 / ac;
                         cs = (R)1 / sqrt((R)1 + t * t);
                         sn = t * cs;
-                        cp = c.x / ac;
-                        spp = c.y / ac;
+                        cp = c.x * rac;
+                        spp = c.y * rac;
                     }
                 }
                 rot[4 * i] = cs; rot[4 * i + 1] = sn; rot[4 * i + 2] = cp; rot[4 * i + 3] = spp;
@@ -1827,8 +1838,10 @@ lsw_status gemm(char opA, char opB, int m, int n, int k, typename Cx<R>::T alpha
     // split K when the output grid alone cannot fill the GPU
     int ksplit = 1;
     const long long ctas = (long long)gx * gy * batch;
-    if (ctas < 304 && k >= 512) {
-        ksplit = (int)std::min<long long>((608 + ctas - 1) / ctas, (k + 255) / 256);
+    if (ctas < 304 && k >= 256) {
+        // chunks of at least 64: a few small outputs (the recompressions'
+        // projections on the inversion's critical path) still fill the GPU
+        ksplit = (int)std::min<long long>((608 + ctas - 1) / ctas, (k + 63) / 64);
         ksplit = std::max(1, std::min(ksplit, 64));
     }
     if (ksplit == 1) {
