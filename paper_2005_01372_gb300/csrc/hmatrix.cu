@@ -655,15 +655,26 @@ lsw_status lr_launch(const LrLevels<C, FT>& lv, int m, int r, int k, const C* X,
     // BF16 factors and complex64 vectors: on the tensor cores when the shapes allow
     bool tc = false;
     if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value) tc = lr_tc_fits(lv, m, r, k);
-    if (tc) {
-        if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value)
-            LSW_TRY(lr_partial_tc(lv, m, r, k, X, swapA, P.as<C>(), st));
-    } else {
-        k_lr_partial<C, FT><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
+    {
+        // every level's first factor once and X once per level
+        KTimer ktp("lr_partial", st, (double)lv.nlev * m * ((double)r * sizeof(FT) + (double)k * sizeof(C)),
+                   8.0 * lv.nlev * (double)m * r * k);
+        if (tc) {
+            if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value)
+                LSW_TRY(lr_partial_tc(lv, m, r, k, X, swapA, P.as<C>(), st));
+        } else {
+            k_lr_partial<C, FT><<<lv.chunk0[lv.nlev], 256, smem, st>>>(lv, m, r, k, X, swapA, P.as<C>());
+            LSW_LAUNCH_CHECK();
+        }
+    }
+    {
+        KTimer ktr("lr_reduce", st, sizeof(C) * (double)(lv.chunk0[lv.nlev] + lv.t0[lv.nlev]) * nout, 0.0);
+        k_lr_reduce<C, FT><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
         LSW_LAUNCH_CHECK();
     }
-    k_lr_reduce<C, FT><<<gridn(lv.t0[lv.nlev] * nout), 256, 0, st>>>(lv, r, k, P.as<C>(), T.as<C>());
-    LSW_LAUNCH_CHECK();
+    // every level's second factor once, Y read and written
+    KTimer kta("lr_apply", st, (double)lv.nlev * m * r * sizeof(FT) + 2.0 * m * k * sizeof(C),
+               8.0 * lv.nlev * (double)m * r * k);
     if (tc) {
         if constexpr (std::is_same<C, float2>::value && std::is_same<FT, uint32_t>::value)
             return lr_apply_tc(lv, m, r, k, T.as<C>(), swapC, Y, st);
