@@ -138,8 +138,10 @@ template <typename R> struct LeafUpd {
 // only the whole-matrix product runs on this storage.
 struct HStoreB {
     int L = 0, r = 0, n = 0;
+    int rp = 0;                       // columns per block of the tiled levels
     uint32_t* D = nullptr;
     std::vector<uint32_t*> U, W;
+    std::vector<int> ulay, wlay;      // FAC_* storage of each level's U and W
     size_t bytes = 0;
     int nl(int l) const { return n >> l; }
     void release() {
@@ -494,6 +496,7 @@ k_lr_partial(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ X, i
     const int row0 = chn * CH;
     const int j = row0 / nb, o = row0 - j * nb;
     const int src = swapA ? (j ^ 1) : j;
+    const int flay = lv.flay[q];
     const FT* Fj = lv.F[q] + (long long)j * nb * r + o;
     const C* Xg = X + (long long)src * nb + o;
     const int mtr = rs / 4, mtk = ks / 4, nmt = mtr * mtk;
@@ -515,7 +518,9 @@ k_lr_partial(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ X, i
         for (int u = 0; u < 8; ++u) {
             const int e = threadIdx.x + u * 256;
             const int cc = e / TR, rr = e - cc * TR;
-            fpre[u] = (e < TR * rs && rr < nr && cc < r) ? ldfac(Fj + (long long)cc * nb + r0 + rr) : czero<C>();
+            const FT* fp = flay == FAC_PLAIN ? Fj + (long long)cc * nb + r0 + rr
+                                             : lv.F[q] + fac_index(flay, nb, r, lv.rp, j, o + r0 + rr, cc);
+            fpre[u] = (e < TR * rs && rr < nr && cc < r) ? ldfac(fp) : czero<C>();
             xpre[u] = (e < TR * ks && rr < nr && cc < k) ? Xg[(long long)cc * m + r0 + rr] : czero<C>();
         }
     };
@@ -607,13 +612,16 @@ k_lr_apply(LrLevels<C, FT> lv, int m, int r, int k, const C* __restrict__ T, int
         const int nb = lv.nb[q];
         const int b = i0 / nb, o = i0 - b * nb;
         const int bb = swapC ? (b ^ 1) : b;
+        const int glay = lv.glay[q];
         const FT* Gb = lv.G[q] + (long long)bb * nb * r + o;
         const C* Tb = T + (lv.t0[q] + bb) * nout;
 #pragma unroll UNR
         for (int t = 0; t < r; ++t) {
             C gv[4], tv[8];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) gv[a] = ldfac(Gb + (long long)t * nb + a);
+            for (int a = 0; a < 4; ++a)
+                gv[a] = ldfac(glay == FAC_PLAIN ? Gb + (long long)t * nb + a
+                                                : lv.G[q] + fac_index(glay, nb, r, lv.rp, bb, o + a, t));
 #pragma unroll
             for (int u = 0; u < 8; ++u) tv[u] = c0 + u < k ? Tb[(long long)(c0 + u) * r + t] : czero<C>();
 #pragma unroll
@@ -1110,6 +1118,21 @@ lsw_status build_smw(const lsw_green* g, const double* chi, const lsw_hparams* h
     return LSW_OK;
 }
 
+// A level's factor (blocks of nb x r, column-major) into BF16 pairs in the
+// storage lay (FAC_*), rp columns per block (the columns beyond r zero).
+__global__ void k_to_bf16_fac(const float2* __restrict__ src, uint32_t* __restrict__ dst, int lay, int nb, int r,
+                              int rp, long long nblk) {
+    const long long tot = nblk * nb * rp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e / ((long long)nb * rp);
+        const long long q = e - j * nb * rp;
+        const int i = (int)(q / nb), o = (int)(q - (long long)i * nb);
+        const float2 v = i < r ? src[(j * r + i) * nb + o] : make_float2(0.f, 0.f);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+        dst[fac_index(lay, nb, r, rp, (int)j, o, i)] = *reinterpret_cast<const uint32_t*>(&b);
+    }
+}
+
 __global__ void k_to_bf16(const float2* __restrict__ src, uint32_t* __restrict__ dst, long long n) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const __nv_bfloat162 v = __floats2bfloat162_rn(src[e].x, src[e].y);
@@ -1148,15 +1171,32 @@ lsw_status to_bf16(const HStore<float>& H, HStoreB& B, cudaStream_t st) {
     LSW_LAUNCH_CHECK();
     B.U.assign(H.L + 1, nullptr);
     B.W.assign(H.L + 1, nullptr);
+    B.ulay.assign(H.L + 1, FAC_PLAIN);
+    B.wlay.assign(H.L + 1, FAC_PLAIN);
+    // levels whose blocks the tensor-core kernels take are stored as their
+    // operand tiles: W for the partials W^H x, U for the products U t
+    B.rp = (H.r + 7) & ~7;
     for (int l = 1; l <= H.L; ++l) {
-        if (cudaMalloc(&B.U[l], sizeof(uint32_t) * nf) != cudaSuccess ||
-            cudaMalloc(&B.W[l], sizeof(uint32_t) * nf) != cudaSuccess)
+        const int nb = H.nl(l);
+        const bool tiled = nb % 128 == 0 && B.rp <= 64;
+        const long long nfl = tiled ? (long long)H.n * B.rp : nf;
+        if (cudaMalloc(&B.U[l], sizeof(uint32_t) * nfl) != cudaSuccess ||
+            cudaMalloc(&B.W[l], sizeof(uint32_t) * nfl) != cudaSuccess)
             return LSW_ERR_OOM;
-        B.bytes += 2 * sizeof(uint32_t) * nf;
-        k_to_bf16<<<gridn(nf), 256, 0, st>>>(H.U[l], B.U[l], nf);
-        LSW_LAUNCH_CHECK();
-        k_to_bf16<<<gridn(nf), 256, 0, st>>>(H.W[l], B.W[l], nf);
-        LSW_LAUNCH_CHECK();
+        B.bytes += 2 * sizeof(uint32_t) * nfl;
+        if (tiled) {
+            B.ulay[l] = FAC_TILE_A;
+            B.wlay[l] = FAC_TILE_P;
+            k_to_bf16_fac<<<gridn(nfl), 256, 0, st>>>(H.U[l], B.U[l], FAC_TILE_A, nb, H.r, B.rp, H.n / nb);
+            LSW_LAUNCH_CHECK();
+            k_to_bf16_fac<<<gridn(nfl), 256, 0, st>>>(H.W[l], B.W[l], FAC_TILE_P, nb, H.r, B.rp, H.n / nb);
+            LSW_LAUNCH_CHECK();
+        } else {
+            k_to_bf16<<<gridn(nf), 256, 0, st>>>(H.U[l], B.U[l], nf);
+            LSW_LAUNCH_CHECK();
+            k_to_bf16<<<gridn(nf), 256, 0, st>>>(H.W[l], B.W[l], nf);
+            LSW_LAUNCH_CHECK();
+        }
     }
     LSW_CUDA(cudaStreamSynchronize(st));
     return LSW_OK;
@@ -1184,14 +1224,17 @@ lsw_status hmv_bf16(const HStoreB& B, const float2* X, int k, float2* Y, cudaStr
         const int kc = std::min(kb, k - c0);
         LrLevels<float2, uint32_t> lv;
         lv.nlev = L;
+        lv.rp = B.rp;
         lv.chunk0[0] = 0;
         lv.t0[0] = 0;
         for (int q = 0; q < L; ++q) {
             const int lp = 1 + q, cnt = 1 << lp, nb = B.nl(lp);
             lv.F[q] = B.W[lp];
             lv.G[q] = B.U[lp];
+            lv.flay[q] = B.wlay[lp];
+            lv.glay[q] = B.ulay[lp];
             lv.nb[q] = nb;
-            lv.ch[q] = std::min(nb, 1024);
+            lv.ch[q] = std::min(nb, 2048);
             lv.chunk0[q + 1] = lv.chunk0[q] + n / lv.ch[q];
             lv.t0[q + 1] = lv.t0[q] + cnt;
         }

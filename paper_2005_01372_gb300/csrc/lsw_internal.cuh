@@ -273,7 +273,32 @@ template <typename C, typename FT = C> struct LrLevels {
     int chunk0[kMaxLev + 1];        // first chunk of each level
     long long t0[kMaxLev + 1];      // first T block of each level (units of r*k)
     int nlev;
+    int flay[kMaxLev] = {};         // storage of F and G per level (FAC_*)
+    int glay[kMaxLev] = {};
+    int rp = 0;                     // columns per block of the tiled storages
 };
+
+// Storage of a level's factor (a block of nb rows and r columns):
+//   FAC_PLAIN: column-major, block after block (nb * r entries each);
+//   FAC_TILE_P: the operand tiles of the partial products F^H x: per block,
+//     per group of 8 rows, the rp columns (r rounded up to 8, zero-padded)
+//     as 8-column x 16-byte core matrices (4 rows of complex per 16 bytes);
+//   FAC_TILE_A: the operand tiles of the products G t: per block, per tile
+//     of 128 rows, per group of 8 columns, the 128 rows as 8-row x 16-byte
+//     core matrices (4 columns of complex per 16 bytes).
+// Either tile is the canonical K-major, non-swizzled tensor-core layout of a
+// 16-element BF16 K-step (two core matrices 128 B apart along K, 8-row
+// groups 256 B apart), so a stage of the tensor-core kernels is one
+// contiguous copy.
+enum { FAC_PLAIN = 0, FAC_TILE_P = 1, FAC_TILE_A = 2 };
+__host__ __device__ __forceinline__ long long fac_index(int lay, int nb, int r, int rp, int j, int o, int i) {
+    if (lay == FAC_PLAIN) return ((long long)j * r + i) * nb + o;
+    const long long base = (long long)j * nb * rp;
+    if (lay == FAC_TILE_P)
+        return base + (long long)(o >> 3) * (rp * 8) + (i >> 3) * 64 + ((o & 7) >> 2) * 32 + (i & 7) * 4 + (o & 3);
+    return base + ((long long)(o >> 7) * (rp >> 3) + (i >> 3)) * 1024 + ((o & 127) >> 3) * 64 + ((i & 7) >> 2) * 32 +
+           (o & 7) * 4 + (i & 3);
+}
 // tcgen05 forms for BF16 factors (lr_tc.cu): the partials P = F^H X per
 // chunk, and Y += sum over levels of G T.
 bool lr_tc_fits(const LrLevels<float2, uint32_t>& lv, int m, int r, int k);

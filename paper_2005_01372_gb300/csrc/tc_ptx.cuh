@@ -27,6 +27,33 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
            (1ull << 46);
 }
 
+// the same with the 8-row stride given: tiles of one 16-element K-step
+// (two core matrices 128 B apart along K, 8-row groups sbo bytes apart)
+__device__ __forceinline__ uint64_t sdesc_sbo(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// byte offset of (row, kgroup) in a one-K-step tile (kgroup 0 or 1)
+__device__ __forceinline__ int kstep_off(int row, int kg) { return (row >> 3) * 256 + kg * 128 + (row & 7) * 16; }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+// one arrival that also announces `bytes` of asynchronous copies
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> shared (addresses 16-byte aligned, bytes a multiple of
+// 16), completing `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 // instruction descriptor: D F32, A and B of one type (1 BF16, 2 TF32), both
 // K-major, N / 8 at bits 17-22, M / 16 at bits 24-28
 __host__ __device__ constexpr uint32_t idesc(uint32_t ab, int M, int N) {

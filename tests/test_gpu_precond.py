@@ -334,8 +334,9 @@ def test_hodlr_power_iteration_parity_c128(lsw):
     assert _rel(y, ref.apply(x.T).T) < 1e-10
 
 
-@pytest.mark.parametrize("n,L,k", [(64, 2, 32), (64, 2, 40), (32, 4, 5), (128, 4, 16)])
-def test_bf16_storage_matches_fp32_storage(lsw, n, L, k):
+@pytest.mark.parametrize("n,L,k,rank", [(64, 2, 32, 12), (64, 2, 40, 12), (32, 4, 5, 12), (128, 4, 16, 12),
+                                         (128, 4, 16, 16), (32, 4, 5, 16), (64, 2, 7, 40)])
+def test_bf16_storage_matches_fp32_storage(lsw, n, L, k, rank):
     """H built in FP32 and kept as BF16 (re, im) pairs: every stored entry is
     rounded to 8 significant bits (relative error <= 2^-9 ~ 2e-3), and the
     leaf inverses' cancellation amplifies that about tenfold in the product,
@@ -343,12 +344,18 @@ def test_bf16_storage_matches_fp32_storage(lsw, n, L, k):
     and clearly away from it (> 1e-5: the factors really are rounded).  At
     n = 64 the leaves (1024 rows) run on the tensor cores (kind::f16); at
     n = 32 with 4 levels (64-row leaves) on the CUDA cores, and the two
-    engines on BF16 storage agree to FP32 accuracy.  The storage takes about half the bytes."""
+    engines on BF16 storage agree to FP32 accuracy.  Levels whose blocks are
+    multiples of 128 rows are stored as the tensor cores' operand tiles, with
+    the rank padded to a multiple of 8 (rank 16 and 40: no padding; the
+    levels of 64-row blocks stay column-major, so the CUDA-core path reads
+    both storages in one matrix).  The storage takes about half the bytes,
+    times the padding at most."""
     P, G, chi = _setup(lsw, n, n, seed=17, freq=12.0)
-    hp = dict(kind=lsw.H_HODLR, levels=L, rank=12, oversample=6, seed=41)
+    hp = dict(kind=lsw.H_HODLR, levels=L, rank=rank, oversample=6, seed=41)
     H32 = lsw.build_hmatrix(G, chi, lsw.HParams(prec=lsw.C64, **hp))
     H16 = lsw.build_hmatrix(G, chi, lsw.HParams(prec=lsw.BF16, **hp))
-    assert H16.nbytes() < 0.51 * H32.nbytes()
+    pad = ((rank + 7) // 8 * 8) / rank
+    assert H16.nbytes() < 0.51 * pad * H32.nbytes()
     rng = np.random.default_rng(3)
     x = torch.from_numpy(media.complex_field(rng, (k, n * n)).astype(np.complex64)).cuda()
     y32 = lsw.apply_precond(H32, x).cpu().numpy()
