@@ -33,8 +33,8 @@ namespace {
 using namespace tcx;
 
 constexpr int LM = 128;                        // MMA rows (TMEM lanes)
-constexpr int LKC = 32;                        // complex K per partial stage
-constexpr int XPAD = 272;                      // smem stride of a raw column of 32 complex (256 B + 16)
+constexpr int LKC = 64;                        // rows (complex K) per partial stage
+constexpr int XPAD = LKC * 8 + 16;             // smem stride of a raw column of a stage (+16 B: no bank conflicts)
 
 __device__ int g_lr_tc_timeouts = 0;
 
@@ -152,24 +152,27 @@ __device__ __forceinline__ bool acc_load(const Ring& g, uint32_t tmem, int li, f
 
 // ------------------------------------------------------------- partials
 // Work item w = chunk w of the level list (chunk0 numbering): CH rows of one
-// level, in stages of 32 rows.  A stage's A'' (rows = the rp factor columns,
-// K = the 32 rows) is one contiguous copy of rp x 128 bytes of the tiled F;
-// the MMA's rows rp..127 read whatever follows in shared memory and land in
-// accumulator rows that are never read.  X's 32 rows of each of the k columns
-// are copied raw (256 B each).  Warp 0 keeps ns stages in flight and refills
-// the slot of stage g - 2, whose MMAs every thread has seen complete.
+// level, in stages of LKC = 64 rows.  A stage's A'' (rows = the rp factor
+// columns, K = the 64 rows: eight K-step tiles) is one contiguous copy of
+// rp x 256 bytes of the tiled F; the MMA's rows rp..127 read whatever follows
+// in shared memory and land in accumulator rows that are never read.  X's 64
+// rows of each of the k columns are copied raw (512 B each) and become B''
+// hi/lo in K-step tiles of 2 NH rows.  Warp 0 keeps ns stages in flight and
+// refills the slot of stage g - 2, whose MMAs every thread has seen complete.
 template <int NH>
 __global__ void __launch_bounds__(128)
 k_lr_partial_tc(LrLevels<float2, uint32_t> lv, int m, int r, int k, const float2* __restrict__ X, int swapA,
                 float2* __restrict__ P, int ns) {
     constexpr int N = 2 * NH;
     constexpr uint32_t ID = idesc(1, LM, N);
-    constexpr int LBP = N * 2 * LKC * 2;               // B'' bytes of a stage (hi or lo)
+    constexpr int KSP = LKC / 8;                       // K-steps per stage
+    constexpr int KB = N * 32;                         // B'' bytes of one K-step
+    constexpr int LBP = KSP * KB;                      // B'' bytes of a stage (hi or lo)
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwork = lv.chunk0[lv.nlev];
     const int rp = lv.rp;
-    const uint32_t SA = (uint32_t)rp * 128;
+    const uint32_t SA = (uint32_t)rp * 4 * LKC;
     const int SAS = (int)((SA + 1023) & ~1023u);
     const int XS = k * XPAD;
     unsigned char* Abuf = sm;
@@ -200,10 +203,11 @@ k_lr_partial_tc(LrLevels<float2, uint32_t> lv, int m, int r, int k, const float2
         const int nb = lv.nb[ii.q];
         const uint32_t* Asrc = lv.F[ii.q] + fac_index(FAC_TILE_P, nb, r, rp, ii.j, ii.o + is * LKC, 0);
         const float2* Xs = X + (long long)ii.src * nb + ii.o + is * LKC;
-        if (lane == 0) mbar_expect_tx(fb, SA + (uint32_t)k * 256u);
+        if (lane == 0) mbar_expect_tx(fb, SA + (uint32_t)k * LKC * 8u);
         __syncwarp();
         if (lane == 0) bulk_g2s(smem_u32(Abuf + (size_t)slot * SAS), Asrc, SA, fb);
-        if (lane < k) bulk_g2s(smem_u32(Xbuf + (size_t)slot * XS + lane * XPAD), Xs + (long long)lane * m, 256u, fb);
+        if (lane < k)
+            bulk_g2s(smem_u32(Xbuf + (size_t)slot * XS + lane * XPAD), Xs + (long long)lane * m, (uint32_t)LKC * 8u, fb);
         ++issued;
         if (++is == ii.S) {
             is = 0;
@@ -234,27 +238,31 @@ k_lr_partial_tc(LrLevels<float2, uint32_t> lv, int m, int r, int k, const float2
         if (gs >= 2 && !mbar_wait(smem_u32(g.mmab + bsel), ((gs - 2) >> 1) & 1)) *g.abort_flag = 1;
         __syncthreads();
         if (*g.abort_flag) break;
-        // B'' of the stage: thread (vector column lane, complex K 8 warp .. + 7)
+        // B'' of the stage: thread (vector column lane, K-steps of warp)
         unsigned char* Bhi = Bbuf + (size_t)bsel * 2 * LBP;
         unsigned char* Blo = Bhi + LBP;
         if (lane < NH) {
-            const float4* xs = reinterpret_cast<const float4*>(Xbuf + (size_t)slot * XS + lane * XPAD + warp * 64);
+            const float4* xs = reinterpret_cast<const float4*>(Xbuf + (size_t)slot * XS + lane * XPAD);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float2 x[4];
+            for (int u = 0; u < KSP / 4; ++u) {
+                const int ks = warp * (KSP / 4) + u;
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const float4 v = lane < k ? xs[2 * h + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x[2 * t] = make_float2(v.x, v.y);
-                    x[2 * t + 1] = make_float2(v.z, v.w);
+                for (int h = 0; h < 2; ++h) {
+                    float2 x[4];
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const float4 v = lane < k ? xs[4 * ks + 2 * h + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        x[2 * t] = make_float2(v.x, v.y);
+                        x[2 * t + 1] = make_float2(v.z, v.w);
+                    }
+                    uint4 rh, rl, ih, il;
+                    b_words(x, 1, rh, rl, ih, il);
+                    const int ob = ks * KB;
+                    *reinterpret_cast<uint4*>(Bhi + ob + kstep_off(lane, h)) = rh;
+                    *reinterpret_cast<uint4*>(Blo + ob + kstep_off(lane, h)) = rl;
+                    *reinterpret_cast<uint4*>(Bhi + ob + kstep_off(lane + NH, h)) = ih;
+                    *reinterpret_cast<uint4*>(Blo + ob + kstep_off(lane + NH, h)) = il;
                 }
-                uint4 rh, rl, ih, il;
-                b_words(x, 1, rh, rl, ih, il);
-                const int kg = 2 * warp + h;
-                *reinterpret_cast<uint4*>(Bhi + kmaj(lane, kg)) = rh;
-                *reinterpret_cast<uint4*>(Blo + kmaj(lane, kg)) = rl;
-                *reinterpret_cast<uint4*>(Bhi + kmaj(lane + NH, kg)) = ih;
-                *reinterpret_cast<uint4*>(Blo + kmaj(lane + NH, kg)) = il;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -264,10 +272,10 @@ k_lr_partial_tc(LrLevels<float2, uint32_t> lv, int m, int r, int k, const float2
             const uint32_t a = smem_u32(Abuf + (size_t)slot * SAS), bh = smem_u32(Bhi), bl = smem_u32(Blo);
             const uint32_t dt = tmem + (uint32_t)((li & 1) * N);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
+            for (int ks = 0; ks < KSP; ++ks) {
                 const uint64_t da = sdesc_sbo(a + ks * rp * 32, 256);
-                mma_bf16(dt, da, sdesc(bh + ks * 256), ID, (cs > 0 || ks > 0) ? 1u : 0u);
-                mma_bf16(dt, da, sdesc(bl + ks * 256), ID, 1u);
+                mma_bf16(dt, da, sdesc_sbo(bh + ks * KB, 256), ID, (cs > 0 || ks > 0) ? 1u : 0u);
+                mma_bf16(dt, da, sdesc_sbo(bl + ks * KB, 256), ID, 1u);
             }
             mma_commit(smem_u32(g.mmab + bsel));
             if (cs == ci.S - 1) mma_commit(smem_u32(g.accf + (li & 1)));
@@ -450,9 +458,9 @@ k_lr_apply_tc(LrLevels<float2, uint32_t> lv, int m, int r, int k, const float2* 
 
 // shared memory of the two kernels for a ring of ns stages
 size_t partial_smem(int NH, int rp, int k, int ns) {
-    const size_t SAS = ((size_t)rp * 128 + 1023) & ~(size_t)1023;
+    const size_t SAS = ((size_t)rp * 4 * LKC + 1023) & ~(size_t)1023;
     const size_t pre = ((size_t)ns * SAS + (size_t)ns * k * XPAD + 1023) & ~(size_t)1023;
-    return pre + 4 * (size_t)(2 * NH) * 2 * LKC * 2 + ring_bytes(ns);
+    return pre + 4 * (size_t)(LKC / 8) * (2 * NH) * 32 + ring_bytes(ns);
 }
 size_t apply_smem(int NH, int r, int rp, int k, int ns) {
     const size_t SA = (size_t)(rp >> 3) * 4096, TS = ((size_t)k * (r * 8 + 16) + 127) & ~(size_t)127;
@@ -490,9 +498,9 @@ lsw_status partial_launch(const LrLevels<float2, uint32_t>& lv, int m, int r, in
                                       (int)cudaSharedmemCarveoutMaxShared));
         attr.store(true);
     }
-    // ring depth: 6 stages, fewer while the CTA does not fit three to an SM
-    int ns = 6;
-    while (ns > 3 && partial_smem(NH, lv.rp, k, ns) > 74 * 1024) --ns;
+    // ring depth: 4 stages, 3 while the CTA does not fit two to an SM
+    int ns = 4;
+    if (partial_smem(NH, lv.rp, k, ns) > 112 * 1024) ns = 3;
     const size_t smem = partial_smem(NH, lv.rp, k, ns);
     int grid = 0;
     LSW_TRY(persistent_grid(smem, 4 * NH, lv.chunk0[lv.nlev], grid));
