@@ -340,6 +340,8 @@ lsw_status fgmres_run(const lsw_green* g, const double* chi, const lsw_hmatrix* 
             // norm of what is left: the coefficients of both passes and the
             // norms come back to the host together, one wait per iteration
             std::vector<Z> hsum((size_t)nb * (j + 1), 0.0);
+            // per pass the basis is read twice and w three times
+            KTimer kt_gs("arnoldi_gs", st, sizeof(C) * (double)n * nb * (4.0 * (j + 1) + 7.0), 0.0);
             for (int pass = 0; pass < 2; ++pass) {
                 C* hcp = pass == 0 ? hc.as<C>() : hc2.as<C>();
                 LSW_TRY(gemm<R>('C', 'N', j + 1, 1, (int)n, one_, V.as<C>(), (int)n, n * (m + 1), w.as<C>(), (int)n, n,
