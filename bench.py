@@ -105,17 +105,26 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# The kernel family with the largest share of the step's launch list (see
-# profiles/), timed live with CUDA events on its launching stream.
+# The kernel family with the largest share of the step's serialised launch
+# list (profiles/step_launches_marmousi_1024x1024_16src.md): the truncation's
+# eigen-decompositions (FP32 Jacobi kernels, Rayleigh-Ritz projection),
+# latency-bound; timed live with CUDA events on their launching streams over
+# the timed steps, against the algorithmic 36 k^3 real flops per matrix.
 DOMINANT = "heev"
-DOMINANT_KERNEL = ("heev: FP64-accurate eigen-decomposition of the sketches' Gram matrices (FP32 Jacobi, "
-                   "FP64-accurate Rayleigh-Ritz projection, FP32 Jacobi on the projection)")
+DOMINANT_KERNEL = ("heev: eigen-decompositions of the sketches' k x k Gram matrices for the truncation (FP32 "
+                   "Jacobi, FP64-accurate Rayleigh-Ritz projection, FP32 Jacobi polish; k = 50), 36 k^3 flops each")
 # DRAM bytes (read + write) per launch of the dominant family from one ncu
 # capture of this workload's step, or None when not captured for this build.
 DOMINANT_TRAFFIC_PER_LAUNCH = None
+# The largest bandwidth-bound kernel of the step: the level partials of the
+# BF16 H apply (k_lr_partial_tc), timed over whole H applies after the timed
+# steps, L2 flushed between applies.
+SOLVE_KERNEL = ("k_lr_partial_tc: every level's W^H x partials of the BF16 HODLR apply (tcgen05, bulk-copy "
+                "ring), 16 vectors at 1024^2")
 # DRAM bytes of one 16-field 1024^2 FP32 RESIDUAL apply (passes k_fa, k_fb,
-# k_fc), from one ncu capture (profiles/fft_operator_passes_1024x1024_c64.md).
-OPERATOR_TRAFFIC = None
+# k_fc: 369 + 489 + 516 MB), from one ncu capture
+# (profiles/fft_operator_passes_1024x1024_c64.md).
+OPERATOR_TRAFFIC = 1.3735e9
 
 
 def fp32_alu_peak_tflops(sms: int = 152, sm_mhz: float = 2070.0) -> float:
@@ -261,14 +270,34 @@ def run_ours(args):
     lsw.kernel_timer_stop()
     fp32_peak = lsw.measure_peak(0)
 
+    # ---- the level partials of the H apply, timed over whole applies
+    H = lsw.build_hmatrix(G, chi, hp)
+    xs = G.point_sources(wl.sources, lsw.C64)
+    ys = torch.empty_like(xs)
+    lsw.apply_precond(H, xs, ys)
+    torch.cuda.synchronize()
+    lsw.kernel_timer_start("lr_partial")
+    for _ in range(20):
+        flush.zero_()
+        lsw.apply_precond(H, xs, ys)
+    lp_ms, lp_bytes, lp_flops, lp_n = lsw.kernel_timer_read()
+    lsw.kernel_timer_stop()
+    del H
+
     peak, peak_kind = load_peaks()
     dom_gbs = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     dom_tf = dom_flops / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else 0.0
-    roof = {"kernel": DOMINANT_KERNEL, "bound": "alu", "achieved": round(dom_tf, 4), "peak": round(fp32_peak, 2),
+    roof = {"kernel": DOMINANT_KERNEL, "bound": "alu", "achieved": round(dom_tf, 5), "peak": round(fp32_peak, 2),
             "peak_kind": "measured: lsw_measure_peak FP32 FMA probe on this device", "unit": "TFLOP/s",
-            "frac": round(dom_tf / fp32_peak, 5) if fp32_peak > 0 else None, "traffic": DOMINANT_TRAFFIC_PER_LAUNCH,
+            "frac": round(dom_tf / fp32_peak, 6) if fp32_peak > 0 else None, "traffic": DOMINANT_TRAFFIC_PER_LAUNCH,
             "launches": int(dom_n), "avg_launch_ms": round(dom_ms / max(1, dom_n), 4),
-            "achieved_gbs": round(dom_gbs, 2), "hbm_frac": round(dom_gbs / peak, 6)}
+            "achieved_gbs": round(dom_gbs, 3), "hbm_frac": round(dom_gbs / peak, 6)}
+    lp_avg = lp_ms / max(1, lp_n)
+    lp_gbs = lp_bytes / (lp_ms / 1e3) / 1e9 if lp_ms > 0 else 0.0
+    lp_roof = {"kernel": SOLVE_KERNEL, "bound": "hbm", "achieved": round(lp_gbs, 1), "peak": peak,
+               "peak_kind": peak_kind, "unit": "GB/s", "frac": round(lp_gbs / peak, 4) if peak else None,
+               "traffic": None, "launches": int(lp_n), "avg_launch_ms": round(lp_avg, 4),
+               "algorithmic_bytes_per_launch": round(lp_bytes / max(1, lp_n))}
     op_tf = op_flops / (op_ms / 1e3) / 1e12 if op_ms > 0 else 0.0
     op_gbs = op_bytes / (op_ms / 1e3) / 1e9 if op_ms > 0 else 0.0
     op_avg = op_ms / max(1, op_n)
@@ -297,7 +326,7 @@ def run_ours(args):
                            "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas{world}"},
                 "solves_converged": int(solves), "max_rel_residual": worst,
                 "operator_applies_per_solve": round(float(np.mean(applies)), 1),
-                "roofline": roof, "operator_roofline": op_roof,
+                "roofline": roof, "solve_roofline": lp_roof, "operator_roofline": op_roof,
                 "e2e": {"value": round(e2e_value, 4), "unit": "solves/s",
                         "h2d_bytes_per_step": int(vel_host.numel() * 8),
                         "d2h_bytes_per_step": int(out_host.numel() * 16)},

@@ -41,6 +41,7 @@ struct TimerState {
     char family[64] = {0};
     bool on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<TimedSpan> captured;     // recorded into a graph being captured
     double ms = 0, bytes = 0, flops = 0;
     unsigned long long launches = 0;
 } g_timer;
@@ -60,25 +61,68 @@ void drain_timer() {
 KTimer::KTimer(const char* family, cudaStream_t st, double bytes, double flops) {
     std::lock_guard<std::mutex> lk(g_timer.mu);
     if (!g_timer.on || strncmp(family, g_timer.family, sizeof g_timer.family) != 0) return;
-    // work being captured into a graph does not run now: nothing to time
+    // work being captured into a graph runs at each replay: its events
+    // become nodes of the graph (see timer_take_captured)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return;
+    captured_ = cs != cudaStreamCaptureStatusNone;
     st_ = st;
     bytes_ = bytes;
     flops_ = flops;
     cudaEventCreate(&e0_);
     cudaEventCreate(&e1_);
-    cudaEventRecord(e0_, st_);
+    // inside a capture, an external record node: the event is recorded at
+    // every replay (a plain record would only order the capture's streams)
+    cudaEventRecordWithFlags(e0_, st_, captured_ ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 KTimer::~KTimer() {
     if (!e0_) return;
-    cudaEventRecord(e1_, st_);
+    cudaEventRecordWithFlags(e1_, st_, captured_ ? cudaEventRecordExternal : cudaEventRecordDefault);
     std::lock_guard<std::mutex> lk(g_timer.mu);
+    if (captured_) {
+        g_timer.captured.push_back(TimedSpan{e0_, e1_, bytes_, flops_});
+        return;
+    }
     g_timer.pending.emplace_back(e0_, e1_);
     g_timer.bytes += bytes_;
     g_timer.flops += flops_;
     g_timer.launches += 1;
+}
+
+std::vector<TimedSpan> timer_take_captured() {
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    std::vector<TimedSpan> v;
+    v.swap(g_timer.captured);
+    return v;
+}
+
+// After a replay of the graph that holds the spans has finished: add each
+// span's elapsed time (while the timer is still on).
+void timer_harvest(const std::vector<TimedSpan>& spans) {
+    if (spans.empty()) return;
+    std::lock_guard<std::mutex> lk(g_timer.mu);
+    if (!g_timer.on) return;
+    for (const auto& sp : spans) {
+        float t = 0;
+        cudaEventSynchronize(sp.e1);
+        if (cudaEventElapsedTime(&t, sp.e0, sp.e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        g_timer.ms += t;
+        g_timer.bytes += sp.bytes;
+        g_timer.flops += sp.flops;
+        g_timer.launches += 1;
+    }
+}
+
+void timer_release(std::vector<TimedSpan>& spans) {
+    for (auto& sp : spans) {
+        cudaEventDestroy(sp.e0);
+        cudaEventDestroy(sp.e1);
+    }
+    spans.clear();
 }
 
 namespace {

@@ -78,6 +78,10 @@ bool graphs_enabled();
 // family named at lsw_kernel_timer_start is enabled, a KTimer records CUDA
 // events on the launching stream around the launches it scopes and adds the
 // algorithmic bytes and flops its caller states.
+// Work captured into a CUDA graph is timed too: the events are recorded as
+// nodes of the graph, the owner of the graph takes them with
+// timer_take_captured() when the capture ends and adds each replay's elapsed
+// times with timer_harvest() once the replay has finished.
 class KTimer {
   public:
     KTimer(const char* family, cudaStream_t st, double bytes, double flops);
@@ -87,7 +91,15 @@ class KTimer {
     cudaEvent_t e0_ = nullptr, e1_ = nullptr;
     cudaStream_t st_ = nullptr;
     double bytes_ = 0, flops_ = 0;
+    bool captured_ = false;
 };
+struct TimedSpan {
+    cudaEvent_t e0, e1;
+    double bytes, flops;
+};
+std::vector<TimedSpan> timer_take_captured();
+void timer_harvest(const std::vector<TimedSpan>& spans);
+void timer_release(std::vector<TimedSpan>& spans);
 
 inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }

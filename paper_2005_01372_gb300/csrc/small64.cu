@@ -540,7 +540,10 @@ lsw_status chol_rinv(const double2* G, int k, int batch, double shift_rel, typen
 lsw_status heev_c64(const double2* G, float2* V, int k, int batch, cudaStream_t st) {
     if (batch <= 0 || k <= 0) return LSW_OK;
     if (k > 64) return LSW_ERR_INVALID_ARG;
-    KTimer kt("heev", st, 0.0, 0.0);
+    // algorithmic work: the classical count of a Hermitian eigen-decomposition
+    // with eigenvectors, 9 k^3 real flops for real symmetric, four times that
+    // for complex (reads and writes of the k x k matrices only, in bytes)
+    KTimer kt("heev", st, 24.0 * (double)k * k * batch, 36.0 * (double)k * k * k * batch);
     const size_t kk = (size_t)k * k;
     DevBuf V0, B, Z;
     LSW_TRY(V0.alloc(sizeof(float2) * kk * batch, st));

@@ -185,7 +185,11 @@ struct StepGraph {
     int runs = 0;
     bool failed = false;
     long long launches = 0;
+    std::vector<TimedSpan> spans;              // timer events inside the graph
+    bool unharvested = false;
     ~StepGraph() {
+        if (unharvested) timer_harvest(spans);
+        timer_release(spans);
         if (exec) cudaGraphExecDestroy(exec);
         if (in) cudaEventDestroy(in);
         if (out) cudaEventDestroy(out);
@@ -217,11 +221,13 @@ struct StepGraph {
         cudaGraph_t gr = nullptr;
         const cudaError_t e = cudaStreamEndCapture(cs, &gr);
         launches = (long long)(launch_counter() - l0);
+        spans = timer_take_captured();
         if (s == LSW_OK && e == cudaSuccess && gr && cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) exec = nullptr;
         if (gr) cudaGraphDestroy(gr);
         cudaGetLastError();
         if (!exec) {
             // nothing captured ran: take back its count and run it eagerly
+            timer_release(spans);
             failed = true;
             count_launches(-launches);
             return body(st);
@@ -232,6 +238,9 @@ struct StepGraph {
 
   private:
     lsw_status replay(cudaStream_t st) {
+        // the previous replay's timer spans (its work is ordered before this one)
+        if (unharvested) timer_harvest(spans);
+        unharvested = !spans.empty();
         LSW_CUDA(cudaEventRecord(in, st));
         LSW_CUDA(cudaStreamWaitEvent(cs, in, 0));
         LSW_CUDA(cudaGraphLaunch(exec, cs));

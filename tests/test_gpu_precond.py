@@ -371,6 +371,38 @@ def test_bf16_storage_matches_fp32_storage(lsw, n, L, k, rank):
     assert _rel(y16, y16cc) < 5e-5
 
 
+def test_kernel_timer_counts_graph_replays(lsw):
+    """A kernel-timer family sees the launches that the Arnoldi step's CUDA
+    graph replays: the operator family counts one application per FGMRES
+    iteration (plus the residuals), with graphs on as with graphs off, and
+    both runs report positive time."""
+    wl = media.gaussian_inclusion_64()
+    P, G, chi = _setup(lsw, 64, 64, velocity=wl.velocity, freq=wl.freq_hz)
+    H = lsw.build_hmatrix(G, chi, lsw.HParams(kind=lsw.H_HODLR, prec=lsw.C64, levels=2, rank=20, oversample=10,
+                                              seed=1001))
+    u0 = G.point_sources([(5, 32), (0, 3)], lsw.C64)
+    sp = lsw.SolveParams(prec=lsw.C64, method=lsw.FGMRES, tol=1e-5, restart=8, max_iter=80)
+    seen = []
+    try:
+        for on in (False, True):
+            lsw.set_graphs(on)
+            torch.cuda.synchronize()
+            g0 = lsw.graph_replay_count()
+            lsw.kernel_timer_start("operator_c64")
+            u, infos = lsw.solve_series(G, chi, H, u0, sp=sp)
+            torch.cuda.synchronize()
+            ms, _, _, n = lsw.kernel_timer_read()
+            lsw.kernel_timer_stop()
+            seen.append((n, ms, lsw.graph_replay_count() - g0, max(i.iterations for i in infos)))
+    finally:
+        lsw.set_graphs(True)
+    (n_off, ms_off, g_off, it_off), (n_on, ms_on, g_on, it_on) = seen
+    assert g_off == 0 and g_on > 0
+    assert it_off == it_on and n_on == n_off
+    assert n_on >= it_on
+    assert ms_off > 0 and ms_on > 0
+
+
 def test_salt_256_bf16_hodlr_fgmres_certified(lsw):
     """The 256 x 256 salt problem with H kept in BF16 inside mixed FGMRES:
     the coarser preconditioner costs iterations, not accuracy; the oracle's
