@@ -106,7 +106,7 @@ class ClockSampler:
 
 
 # The kernel family with the largest share of the step's serialised launch
-# list (profiles/step_launches_marmousi_1024x1024_16src.md): the truncation's
+# list (an ncu capture of one step, gpu__time_duration per launch): the truncation's
 # eigen-decompositions (FP32 Jacobi kernels, Rayleigh-Ritz projection),
 # latency-bound; timed live with CUDA events on their launching streams over
 # the timed steps, against the algorithmic 36 k^3 real flops per matrix.
@@ -122,8 +122,7 @@ DOMINANT_TRAFFIC_PER_LAUNCH = None
 SOLVE_KERNEL = ("k_lr_partial_tc: every level's W^H x partials of the BF16 HODLR apply (tcgen05, bulk-copy "
                 "ring), 16 vectors at 1024^2")
 # DRAM bytes of one 16-field 1024^2 FP32 RESIDUAL apply (passes k_fa, k_fb,
-# k_fc: 369 + 489 + 516 MB), from one ncu capture
-# (profiles/fft_operator_passes_1024x1024_c64.md).
+# k_fc: 369 + 489 + 516 MB), from one ncu capture of three applies.
 OPERATOR_TRAFFIC = 1.3735e9
 
 
