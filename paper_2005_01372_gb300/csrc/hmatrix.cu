@@ -123,6 +123,13 @@ template <typename R> struct HStore {
 template <typename R> struct LeafUpd {
     std::vector<cudaEvent_t> ready;
     std::vector<int> end;
+    // level l's off-diagonal blocks of the matrix being inverted are
+    // sketched once level_done[l] has fired (none: already complete)
+    std::vector<cudaEvent_t> level_done;
+    lsw_status wait_level(int l, cudaStream_t st) const {
+        if (l >= 0 && l < (int)level_done.size() && level_done[l]) LSW_CUDA(cudaStreamWaitEvent(st, level_done[l], 0));
+        return LSW_OK;
+    }
     // make st wait until every leaf up to `last` has its inverse
     lsw_status wait(int last, cudaStream_t st) const {
         for (size_t b = 0; b < end.size(); ++b)
@@ -917,6 +924,9 @@ lsw_status invert_node(HStore<R>& X, int l, int c, HStore<R>& Hi, int oversample
     C* UC = X.U[l + 1] + (size_t)b * nb1;   // C = UC WC^H
     C* WC = X.W[l + 1] + (size_t)b * nb1;
     LSW_TRY(invert_node<R>(X, l + 1, a, Hi, oversample, seed, st, lu));
+    // the first use of level l + 1's blocks (deeper levels were waited for
+    // inside the subtree just inverted, which holds a node of every level)
+    LSW_TRY(lu.wait_level(l + 1, st));
     DevBuf P, Rm, T1, T2, K, XK, T;
     const size_t vb = sizeof(C) * (size_t)m1 * r;
     LSW_TRY(P.alloc(vb, st));
@@ -1014,20 +1024,40 @@ lsw_status build_hodlr(const lsw_green* g, const double* chi, const lsw_hparams*
             first = lu.end[b];
         }
     }
-    {
-        // the levels are independent of each other and of the dense leaves:
-        // sketch them concurrently
-        Fork fk(st);
-        for (int l = 1; l <= L; ++l) {
-            cudaStream_t sl = fk.child(l);
-            KTimer kt("hodlr_level_sketch", sl, 0, 0);
-            LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, spec[l], sl));
+    // The levels are independent of each other and of the dense leaves:
+    // sketch them concurrently, each on a stream of its own, deepest first;
+    // the inversion starts at once and waits for a level only where it
+    // first reads it (the recursion reaches the deep levels first).
+    std::vector<cudaStream_t> lstream(L + 1, nullptr);
+    struct LevelGuard {
+        std::vector<cudaStream_t>* s;
+        std::vector<cudaEvent_t>* e;
+        ~LevelGuard() {
+            for (auto v : *e) if (v) cudaEventDestroy(v);
+            for (auto v : *s) if (v) cudaStreamDestroy(v);
         }
-        LSW_TRY(fk.join());
+    } levelguard{&lstream, &lu.level_done};
+    lu.level_done.assign(L + 1, nullptr);
+    {
+        cudaEvent_t begin;
+        LSW_CUDA(cudaEventCreateWithFlags(&begin, cudaEventDisableTiming));
+        LSW_CUDA(cudaEventRecord(begin, st));
+        for (int l = L; l >= 1; --l) {
+            LSW_CUDA(cudaStreamCreateWithFlags(&lstream[l], cudaStreamNonBlocking));
+            LSW_CUDA(cudaStreamWaitEvent(lstream[l], begin, 0));
+            {
+                KTimer kt("hodlr_level_sketch", lstream[l], 0, 0);
+                LSW_TRY(build_level<R>(g, chi, tr, l, r, rp, hp->q, hp->seed, X, spec[l], lstream[l]));
+            }
+            LSW_CUDA(cudaEventCreateWithFlags(&lu.level_done[l], cudaEventDisableTiming));
+            LSW_CUDA(cudaEventRecord(lu.level_done[l], lstream[l]));
+        }
+        cudaEventDestroy(begin);
     }
     KTimer kti("hodlr_invert", st, 0, 0);
     LSW_TRY(Hi.alloc(L, r, tr.n));
     LSW_TRY(invert_node<R>(X, 0, 0, Hi, hp->oversample, hp->seed, st, lu));
+    for (int l = 1; l <= L; ++l) LSW_TRY(lu.wait_level(l, st));
     LSW_TRY(fkd.join());
     LSW_CUDA(cudaStreamSynchronize(st));
     return LSW_OK;
