@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <atomic>
 #include <cmath>
 #include <map>
@@ -83,6 +84,26 @@ struct Tree {
     }
 };
 
+// Large H-matrix arrays come from the device's stream-ordered pool (which
+// keeps freed memory mapped: the next build of the same size reuses it
+// without new mappings).  The allocation is complete before the call
+// returns; a release first waits for the device, as cudaFree would.
+inline lsw_status pool_alloc(void** p, size_t bytes) {
+    if (cudaMallocAsync(p, bytes, 0) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return LSW_ERR_OOM;
+    }
+    if (cudaStreamSynchronize(0) != cudaSuccess) return LSW_ERR_CUDA;
+    return LSW_OK;
+}
+inline void pool_free_all(std::initializer_list<const std::vector<void*>*> lists) {
+    cudaDeviceSynchronize();
+    for (auto v : lists)
+        for (void* p : *v)
+            if (p) cudaFreeAsync(p, 0);
+}
+
 template <typename R> struct HStore {
     typedef typename Cx<R>::T C;
     int L = 0, r = 0, n = 0;
@@ -94,21 +115,22 @@ template <typename R> struct HStore {
         L = L_; r = r_; n = n_;
         const int nL = nl(L);
         const size_t dbytes = sizeof(C) * (size_t)n * nL;
-        if (cudaMalloc(&D, dbytes) != cudaSuccess) return LSW_ERR_OOM;
+        LSW_TRY(pool_alloc(reinterpret_cast<void**>(&D), dbytes));
         bytes = dbytes;
         U.assign(L + 1, nullptr);
         W.assign(L + 1, nullptr);
         for (int l = 1; l <= L; ++l) {
             const size_t b = sizeof(C) * (size_t)n * r;   // 2^l blocks x n_l x r
-            if (cudaMalloc(&U[l], b) != cudaSuccess || cudaMalloc(&W[l], b) != cudaSuccess) return LSW_ERR_OOM;
+            LSW_TRY(pool_alloc(reinterpret_cast<void**>(&U[l]), b));
+            LSW_TRY(pool_alloc(reinterpret_cast<void**>(&W[l]), b));
             bytes += 2 * b;
         }
         return LSW_OK;
     }
     void release() {
-        if (D) cudaFree(D);
-        for (auto p : U) if (p) cudaFree(p);
-        for (auto p : W) if (p) cudaFree(p);
+        if (!D && U.empty() && W.empty()) return;
+        std::vector<void*> a{D}, u(U.begin(), U.end()), w(W.begin(), W.end());
+        pool_free_all({&a, &u, &w});
         D = nullptr;
         U.clear();
         W.clear();
@@ -152,9 +174,9 @@ struct HStoreB {
     size_t bytes = 0;
     int nl(int l) const { return n >> l; }
     void release() {
-        if (D) cudaFree(D);
-        for (auto p : U) if (p) cudaFree(p);
-        for (auto p : W) if (p) cudaFree(p);
+        if (!D && U.empty() && W.empty()) return;
+        std::vector<void*> a{D}, u(U.begin(), U.end()), w(W.begin(), W.end());
+        pool_free_all({&a, &u, &w});
         D = nullptr;
         U.clear();
         W.clear();
@@ -1195,7 +1217,7 @@ lsw_status to_bf16(const HStore<float>& H, HStoreB& B, cudaStream_t st) {
     B.n = H.n;
     const int nL = H.nl(H.L);
     const long long nd = (long long)H.n * nL, nf = (long long)H.n * H.r;
-    if (cudaMalloc(&B.D, sizeof(uint32_t) * nd) != cudaSuccess) return LSW_ERR_OOM;
+    LSW_TRY(pool_alloc(reinterpret_cast<void**>(&B.D), sizeof(uint32_t) * nd));
     B.bytes = sizeof(uint32_t) * nd;
     k_to_bf16<<<gridn(nd), 256, 0, st>>>(H.D, B.D, nd);
     LSW_LAUNCH_CHECK();
@@ -1210,9 +1232,8 @@ lsw_status to_bf16(const HStore<float>& H, HStoreB& B, cudaStream_t st) {
         const int nb = H.nl(l);
         const bool tiled = nb % 128 == 0 && B.rp <= 64;
         const long long nfl = tiled ? (long long)H.n * B.rp : nf;
-        if (cudaMalloc(&B.U[l], sizeof(uint32_t) * nfl) != cudaSuccess ||
-            cudaMalloc(&B.W[l], sizeof(uint32_t) * nfl) != cudaSuccess)
-            return LSW_ERR_OOM;
+        LSW_TRY(pool_alloc(reinterpret_cast<void**>(&B.U[l]), sizeof(uint32_t) * nfl));
+        LSW_TRY(pool_alloc(reinterpret_cast<void**>(&B.W[l]), sizeof(uint32_t) * nfl));
         B.bytes += 2 * sizeof(uint32_t) * nfl;
         if (tiled) {
             B.ulay[l] = FAC_TILE_A;
