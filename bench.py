@@ -116,11 +116,11 @@ DOMINANT_KERNEL = ("heev: eigen-decompositions of the sketches' k x k Gram matri
 # DRAM bytes (read + write) per launch of the dominant family from one ncu
 # capture of this workload's step, or None when not captured for this build.
 DOMINANT_TRAFFIC_PER_LAUNCH = None
-# The largest bandwidth-bound kernel of the step: the level partials of the
-# BF16 H apply (k_lr_partial_tc), timed over whole H applies after the timed
-# steps, L2 flushed between applies.
-SOLVE_KERNEL = ("k_lr_partial_tc: every level's W^H x partials of the BF16 HODLR apply (tcgen05, bulk-copy "
-                "ring), 16 vectors at 1024^2")
+# The largest bandwidth-bound kernel of the H apply's level products: the
+# partials of the BF16 H apply (k_lr_partial_ws), timed over whole H applies
+# after the timed steps, L2 flushed between applies.
+SOLVE_KERNEL = ("k_lr_partial_ws: every level's W^H x partials of the BF16 HODLR apply (tcgen05, warp-specialised "
+                "bulk-copy ring), 16 vectors at 1024^2")
 # DRAM bytes of one 16-field 1024^2 FP32 RESIDUAL apply (passes k_fa, k_fb,
 # k_fc: 369 + 489 + 516 MB), from one ncu capture of three applies.
 OPERATOR_TRAFFIC = 1.3735e9
