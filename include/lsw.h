@@ -145,17 +145,23 @@ lsw_status lsw_mempool_usage(uint64_t* used_current, uint64_t* used_high, int re
 /* Diagnostic timing of one kernel family inside any call (not part of the
  * method).  lsw_kernel_timer_start(family) resets and enables it for
  * "operator_c64" / "operator_c128" (the three FFT passes of one operator
- * apply in that precision), "qr" (the row
- * chunks of the tall-skinny QR), "gj_update" (the Gauss-Jordan block
- * updates) or "leaf_tc" (the tensor-core products of H's dense leaves);
- * CUDA events are then recorded on the launching stream around
- * each such launch, with the algorithmic bytes and flops of its work.
+ * apply in that precision), "qr" (the thin QR of complex64 sketch blocks),
+ * "gram", "chol", "heev" (the truncation's eigen-decompositions),
+ * "gj_update" (the Gauss-Jordan block updates), "leaf_tc" (the tensor-core
+ * products of H's dense leaves), "lr_levels", "lr_partial", "lr_reduce",
+ * "lr_apply" (the level products of an H apply) or "arnoldi_gs" (the
+ * Gram-Schmidt step of an FGMRES iteration); CUDA events are then recorded on
+ * the launching stream around each such launch, with the algorithmic bytes
+ * and flops of its work.  Launches captured into the solvers' CUDA graphs
+ * are timed too: their events are recorded as nodes of the graph and read
+ * after each replay.
  * Phases of lsw_build_hmatrix (HODLR) time the same way, on the stream that
  * runs them: "hodlr_level_sketch" (one level's sketches), "hodlr_leaf_inverse"
  * (the dense leaves' inverses), "hodlr_invert" (the recursive inversion) and,
  * inside it, "hodlr_add_lowrank" (one low-rank update with its
- * recompressions), "hodlr_leaf_woodbury" (one Schur leaf) and
- * "hodlr_subtree_products" (a pair of subtree products).
+ * recompressions), "hodlr_leaf_woodbury" (one batched Woodbury update of a
+ * node's leaf inverses) and "hodlr_subtree_products" (a pair of subtree
+ * products).
  * lsw_kernel_timer_read waits for the recorded events and reports the sums
  * (any pointer may be NULL). */
 lsw_status lsw_kernel_timer_start(const char* family);
